@@ -1,0 +1,102 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module holds no arithmetic of the method itself: it only describes workloads
+(lattice dimensions, sample counts, temperature sets, seeds).  Both sides receive the
+same doubles for the temperatures, so neither recomputes them.
+
+Temperature sets (Sec. 2.3): the geometric set, a constant ratio between neighbouring
+temperatures, T_k = T_min (T_max/T_min)^(k/(n-1)); the inverse-linear set, constant
+steps in beta; and the phi-family of Eqs. 6-7, T_i = i^phi T_norm + T_min with
+T_norm = (T_max - T_min)/(N_T - 1)^phi.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Sequence
+
+
+def geometric_temps(t_min: float, t_max: float, n: int) -> List[float]:
+    """Geometric temperature set (Sec. 2.3): constant ratio between neighbours."""
+    if n == 1:
+        return [float(t_min)]
+    return [t_min * math.pow(t_max / t_min, k / (n - 1)) for k in range(n)]
+
+
+def inverse_linear_temps(t_min: float, t_max: float, n: int) -> List[float]:
+    """Constant steps in inverse temperature (Sec. 2.3)."""
+    if n == 1:
+        return [float(t_min)]
+    b0, b1 = 1.0 / t_min, 1.0 / t_max
+    return [1.0 / (b0 + (b1 - b0) * k / (n - 1)) for k in range(n)]
+
+
+def phi_temps(t_min: float, t_max: float, n: int, phi: float) -> List[float]:
+    """The phi-family of Eqs. 6-7."""
+    if n == 1:
+        return [float(t_min)]
+    t_norm = (t_max - t_min) / math.pow(n - 1, phi)
+    return [math.pow(i, phi) * t_norm + t_min for i in range(n)]
+
+
+@dataclass
+class Workload:
+    """One simulation job: the parameters the C-ABI's create call takes."""
+
+    name: str
+    ndim: int
+    dims: Sequence[int]
+    n_samples: int
+    n_chains: int
+    temps: Sequence[float]
+    coupling_seed: int = 1
+    sim_seed: int = 1
+    p_plus: float = 0.5
+    spin_format: str = "packed"  # "packed" (32 replicas per word) or "int8"
+    houdayer: bool = False
+    n_mcs: int = 1
+    sample_offset: int = 0
+    notes: str = field(default="")
+
+    @property
+    def N(self) -> int:
+        n = 1
+        for x in self.dims[: self.ndim]:
+            n *= int(x)
+        return n
+
+    @property
+    def T(self) -> int:
+        return len(self.temps)
+
+    @property
+    def replicas(self) -> int:
+        return self.n_samples * self.n_chains * self.T
+
+    @property
+    def attempts_per_sweep(self) -> int:
+        return self.N * self.replicas
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def workload_3d_l6() -> Workload:
+    """3D +-J L=6, 8 samples x 2 chains x 12 geometric temps in [1, 2], int8 spins,
+    200 MCS of Metropolis + PT, seeds 1."""
+    return Workload("3d_L6_S8_T12_int8", 3, (6, 6, 6), 8, 2, geometric_temps(1.0, 2.0, 12),
+                    spin_format="int8", n_mcs=200)
+
+
+def workload_3d_l16() -> Workload:
+    """3D +-J L=16, 1024 samples x 2 chains x 32 geometric temps in [0.9, 2.0],
+    bit-packed spins + 3-bit couplings, 10^4 MCS of Metropolis + PT."""
+    return Workload("3d_L16_S1024_T32_packed", 3, (16, 16, 16), 1024, 2,
+                    geometric_temps(0.9, 2.0, 32), n_mcs=10000)
+
+
+def workload_2d_l128_houdayer() -> Workload:
+    """2D +-J L=128, 256 samples x 2 chains x 24 geometric temps in [0.2, 1.6],
+    Metropolis + Houdayer + PT each MCS, 5000 MCS."""
+    return Workload("2d_L128_S256_T24_houdayer", 2, (128, 128), 256, 2,
+                    geometric_temps(0.2, 1.6, 24), houdayer=True, n_mcs=5000)
