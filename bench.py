@@ -1,0 +1,302 @@
+"""Benchmark: spin-flip attempts per ns of the parallel-tempering Monte Carlo step.
+
+Workload: 3D +-J Edwards-Anderson spin glass, L = 16 periodic, 1024 disorder samples x
+2 chains x 32 geometric temperatures in [0.9, 2.0], bit-packed spins and couplings.
+One step is one MCS over the whole batch: a checkerboard Metropolis sweep of every
+replica (with the energies) and one replica-exchange pass (Eq. 5), i.e. one launch of
+the resident kernel.  Inputs are synthetic (seeded couplings and hot start).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank simulates its own 1024
+samples (job-wide sample offsets rank * 1024), so per-GPU work is fixed: weak scaling.
+`--impl reference` times the CPU oracle (the plain C implementation the tests check the
+engine against) on the host cores, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/ns"
+UNIT = "attempts/ns"
+BYTES_PER_ATTEMPT = 0.25  # 1 bit read + 1 bit written per spin per sweep (packed)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int):
+    """Time the CPU oracle, as it is, on `n_samples` samples of the workload for `n_mcs`
+    MCS each, one oracle per thread (ctypes releases the GIL)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    oracle.build()
+    per = max(1, n_samples // n_threads)
+    shards = [(t * per, per) for t in range(n_threads)]
+
+    def run(shard):
+        off, S = shard
+        o = oracle.Oracle(oracle.OracleParams(workload.ndim, workload.dims, S, workload.n_chains,
+                                              list(workload.temps), coupling_seed=workload.coupling_seed,
+                                              sim_seed=workload.sim_seed, sample_offset=off))
+        o.mcs(n_mcs)
+        return S
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=n_threads) as ex:
+        done = sum(ex.map(run, shards))
+    dt = time.perf_counter() - t0
+    attempts = workload.N * workload.n_chains * workload.T * done * n_mcs
+    return attempts / (dt * 1e9), dt, done
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle on the host cores, same metric and workload."""
+    from paper_2003_04621_gb300.inputs import workload_3d_l16
+
+    if rank != 0:
+        return
+    w = workload_3d_l16()
+    cores = os.cpu_count() or 1
+    samples_per_step = cores
+    for _ in range(args.warmup):
+        cpu_baseline(w, cores, 1, samples_per_step)
+    t0 = time.perf_counter()
+    total_attempts = 0
+    for _ in range(args.steps):
+        _, _, done = cpu_baseline(w, cores, 1, samples_per_step)
+        total_attempts += w.N * w.n_chains * w.T * done
+    dt = time.perf_counter() - t0
+    value = total_attempts / (dt * 1e9)
+    sample = f"{samples_per_step} of the {w.n_samples} samples x 1 MCS per step, one oracle thread per sample"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded couplings and hot start)",
+        "config": {"workload": w.name, "lattice": "3D L=16 periodic", "samples": w.n_samples, "chains": 2,
+                   "temps": 32, "parallelism": "cpu threads over samples"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2003_04621_gb300 import build as _build
+    from paper_2003_04621_gb300.inputs import workload_3d_l16
+    from paper_2003_04621_gb300.sgmc import Simulation
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    w = workload_3d_l16().with_(sample_offset=rank * 1024)
+    stream = torch.cuda.Stream()
+    kw = dict(ndim=w.ndim, dims=w.dims, n_samples=w.n_samples, n_chains=w.n_chains, temps=list(w.temps),
+              coupling_seed=w.coupling_seed, sim_seed=w.sim_seed, sample_offset=w.sample_offset)
+    sim = Simulation(stream=stream, **kw)
+    attempts_per_step = w.attempts_per_sweep
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        sim.run_mcs(1)
+    # the packed state (36 MB) fits in L2 (129 MB): flush L2 between timed steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            sim.run_mcs(1)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = attempts_per_step * ws * args.steps / (total_ms * 1e6)
+    mean_launch_ms = total_ms / args.steps
+
+    # end to end through the public API: create from host parameters, then per step one
+    # MCS and a device->host read of the observables (E by slot and N q)
+    e2e = None
+    if rank == 0 or ws > 1:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = Simulation(stream=stream, **kw)
+        for _ in range(args.steps):
+            sim2.run_mcs(1, stream=stream)
+            E, Q = sim2.measure(stream=stream)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        d2h = E.nbytes + Q.nbytes
+        h2d = (w.T * 8 + w.T * 16) / args.steps
+        e2e = {"value": attempts_per_step * args.steps / (e2e_s * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "includes": "create (H2D tables, device init) + per step one MCS and a D2H read of E and q"}
+        sim2.close()
+
+    pk, pk_kind = peaks()
+    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # ALU roofline: lane-instructions per second at the sampled SM clock (4 schedulers x 32
+    # lanes x 1 instruction per clock per SM), against the algorithmic instructions of an
+    # attempt: Philox4x32-10 costs 10 rounds x (2 wide multiplies + 2 three-input xors) per
+    # 4 words = 10 per attempt, plus the compare and the accept-bit insert = 12.
+    instr_per_attempt = 12.0
+    peak_tips = n_sm * 4 * 32 * sm_mhz * 1e6 / 1e12
+    achieved_tips = attempts_per_step * instr_per_attempt / (mean_launch_ms * 1e-3) / 1e12
+    hbm_eff = attempts_per_step * BYTES_PER_ATTEMPT / (mean_launch_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("resident_packed_3d_l16_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic (seeded +-J couplings and hot start)",
+        "config": {"workload": w.name, "lattice": "3D L=16 periodic", "samples_per_gpu": w.n_samples,
+                   "chains": w.n_chains, "temps": w.T, "temp_range": [0.9, 2.0], "spin_format": "packed32",
+                   "step": "one MCS = checkerboard Metropolis sweep + replica exchange, one fused launch",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"samples x{ws}"},
+        "gpu_launches": args.steps,
+        "wall_s": wall,
+        "clocks": clk,
+        "roofline": {"bound": "alu", "achieved": achieved_tips, "peak": peak_tips, "unit": "Tinstr/s",
+                     "frac": achieved_tips / peak_tips, "traffic": traffic,
+                     "kernel": "k_resident_packed<3,256,fused PT>",
+                     "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled)",
+                     "instr_per_attempt": instr_per_attempt},
+        "hbm_effective": {"achieved_gbs": hbm_eff, "peak_gbs": pk["hbm_gbs"], "frac": hbm_eff / pk["hbm_gbs"],
+                          "peak_kind": pk_kind, "bytes_per_attempt": BYTES_PER_ATTEMPT},
+        "e2e": e2e,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, dt, done = cpu_baseline(w, cores, 40, cores)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{done} of the {w.n_samples} samples x 40 MCS, one oracle thread per "
+                                          f"sample ({dt:.1f} s wall)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

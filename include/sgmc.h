@@ -1,0 +1,168 @@
+/*
+ * sgmc.h -- C-ABI of the GB300 (sm_103a) engine for parallel-tempering Monte Carlo of
+ * +-J Edwards-Anderson Ising spin glasses, after Kumar, Gross, Janke & Weigel,
+ * "Massively parallel simulations for disordered systems" (arXiv:2003.04621).
+ *
+ * The engine simulates n_samples disorder samples x n_chains independent copies x
+ * n_temps temperatures at once (Sec. 3).  Every call below is a plain C function over
+ * host or device pointers and sizes; no C++ or framework types cross the boundary.
+ *
+ * Conventions
+ *   - Every call returns an sg_status.  No call aborts or prints.
+ *   - The handle owns NO device memory: the caller allocates one device buffer of
+ *     sg_query_bytes() bytes and passes it to sg_create(); it must outlive the handle.
+ *   - `stream` is a cudaStream_t cast to uintptr_t (0 = legacy default stream).  All
+ *     device work of a call is enqueued on that stream; calls that return host data say
+ *     so and synchronise that stream.
+ *   - After SG_ECUDA or SG_ETIMEOUT the handle is poisoned: every later call except
+ *     sg_destroy/sg_strerror returns the same status.
+ *   - A handle is not thread-safe; use one stream per handle at a time.
+ *   - Results depend only on the parameters and on the sequence of calls made: never
+ *     on the device, the launch shape, or other handles running alongside.
+ *
+ * Model and readings (Sec. 2.1, Eqs. 1-2, H = 0)
+ *   Lattice: ndim = 2 or 3, extents dims[0..ndim-1] (x fastest), periodic.  Site index
+ *   i = x + L0 (y + L1 z).  Bond (i, mu) joins i and i + e_mu (forward bonds only; on an
+ *   L = 2 axis both bonds between a pair are kept).  Couplings J = +-1 with
+ *   P(J = +1) = p_plus (Eq. 2).  Spin bit 1 <-> s = -1.
+ *   Sweep order: checkerboard, colour (x+y+z) mod 2, colour 0 first; so every extent must
+ *   be even (SG_EUNSUPPORTED otherwise).
+ *   Random numbers: Philox4x32-10 (counter-based, Sec. 3; Salmon et al. 2011), with
+ *     couplings  key = coupling_seed, ctr = (i, mu, s, 4), word 0, J = +1 iff w < floor(p 2^32)
+ *     hot start  key = sim_seed, ctr = (i, 0, s, c<<20 | (j>>2)<<8 | 3), word j&3, top bit
+ *     Metropolis key = sim_seed, ctr = (i, t_metro, s, c<<20 | (j>>2)<<8 | 0), word j&3
+ *     exchange   key = sim_seed, ctr = (k, t_pt, s, c<<20 | 1), word 0
+ *     Houdayer   key = sim_seed, ctr = (k, t_houd, s, 2), word 0
+ *   where s = sample_offset + local sample, c = chain, j = replica within its chain,
+ *   k = temperature slot and t_* = the number of such steps made before.
+ *
+ * Device memory is laid out by the engine inside the caller's buffer (see DESIGN notes
+ * in the repository); callers reach state only through the calls below.
+ */
+#ifndef SGMC_H
+#define SGMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_handle sg_handle; /* opaque host object */
+
+typedef enum {
+  SG_OK = 0,
+  SG_EINVAL = 1,        /* invalid argument (null pointer, bad size, bad parameter)      */
+  SG_ENOMEM = 2,        /* the caller's device buffer is smaller than sg_query_bytes()   */
+  SG_ECUDA = 3,         /* a CUDA call failed; the handle is poisoned                    */
+  SG_ETIMEOUT = 4,      /* a bounded device-side wait expired; the handle is poisoned    */
+  SG_EUNSUPPORTED = 5   /* valid but outside what this engine implements (odd extents,
+                           a lattice too large for the resident kernels, ...)          */
+} sg_status;
+
+enum { SG_PACKED32 = 0, SG_INT8 = 1 };
+
+/* Parameters of one simulation job (Sec. 2; the problem statement of Sec. 2.1-2.4). */
+typedef struct {
+  int32_t ndim;          /* 2 or 3                                                        */
+  int32_t dims[3];       /* L0, L1, L2 (entries >= ndim ignored); each even and >= 2      */
+  int32_t n_samples;     /* disorder samples on this handle, >= 1                         */
+  int32_t sample_offset; /* job-wide index of the first sample; random keys use it, so a
+                            job split over handles (or GPUs) reproduces the whole job     */
+  int32_t n_chains;      /* copies per temperature: 1, or 2 (needed for q and Houdayer;
+                            the paper's N_C = 2, Sec. 2.4)                                */
+  int32_t n_temps;       /* temperatures per chain, >= 1                                  */
+  const double *temps;   /* host, n_temps strictly ascending positive temperatures; the
+                            engine copies them; beta_k = 1.0 / temps[k] in fp64         */
+  uint64_t coupling_seed;
+  double p_plus;         /* P(J = +1) of Eq. 2, in [0, 1]                                 */
+  uint64_t sim_seed;
+  int32_t spin_format;   /* SG_PACKED32: 32 replicas of one site per 32-bit word;
+                            SG_INT8: one int8 +-1 per spin (the paper's layout)           */
+  int32_t houdayer;      /* 1: sg_run_mcs performs one Houdayer move per (sample, slot)   */
+  int32_t n_metro;       /* Metropolis sweeps per MCS (Sec. 2.4 step 1; usually 1), >= 1  */
+  int32_t reserved;      /* must be 0                                                     */
+} sg_params;
+
+/* Bytes of device memory a handle with these parameters needs. */
+sg_status sg_query_bytes(const sg_params *p, size_t *device_bytes);
+
+/* Create a simulation in the caller's device buffer (>= sg_query_bytes bytes, 256-byte
+ * aligned).  Draws the couplings (Eq. 2) and a hot start, computes every energy (Eq. 1)
+ * and sets each chain's temperature map to the identity.  Enqueued on `stream`; the
+ * handle is usable as soon as this returns.  *out receives the handle. */
+sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_t stream,
+                    sg_handle **out);
+
+/* n_sweeps Metropolis sweeps of every replica (Sec. 2.2 and Sec. 2.4 step 1):
+ * single-spin flips, accepted iff dE <= 0 or r < floor(exp(-beta dE) 2^32), r the
+ * replica's Philox word for that site and sweep. */
+sg_status sg_sweep(sg_handle *h, int32_t n_sweeps, uintptr_t stream);
+
+/* One replica-exchange pass (Eq. 5; Sec. 2.4 step 3): in every (sample, chain), for
+ * k = 0..n_temps-2 in order, swap the temperatures of the replicas at slots k and k+1
+ * with probability min[1, exp((1/T_k - 1/T_k+1)(E_k - E_k+1))] (fp64 on the device).
+ * Temperatures, not configurations, are exchanged (two maps, Sec. 3). */
+sg_status sg_exchange(sg_handle *h, uintptr_t stream);
+
+/* One Houdayer cluster move (Sec. 2.4, Eq. 10) for every (sample, temperature slot):
+ * the chain-0 and chain-1 replicas at that slot exchange their spins on the connected
+ * q = -1 cluster grown from the floor(u M / 2^32)-th q = -1 site (M = number of such
+ * sites; no move if M = 0).  Needs n_chains == 2. */
+sg_status sg_houdayer(sg_handle *h, uintptr_t stream);
+
+/* n_mcs Monte Carlo steps (Sec. 2.4): n_metro sweeps, then (if houdayer) one Houdayer
+ * move per pair, then one exchange pass.  Identical to the same sequence of the three
+ * calls above. */
+sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream);
+
+/* Observables (Eqs. 3-4) into HOST buffers; synchronises `stream`.
+ *   E_out [n_samples][n_chains][n_temps]  energy of the replica at each slot
+ *   Q_out [n_samples][n_temps]            N q = sum_i s_i^(a) s_i^(b), a/b the chain-0 and
+ *                                         chain-1 replicas at the slot (may be NULL;
+ *                                         ignored if n_chains == 1) */
+sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
+
+/* As sg_measure, into DEVICE buffers of the same shapes, without synchronising. */
+sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
+
+/* Spins in a plain layout, DEVICE buffers: uint8 [n_samples][n_chains][n_temps][N],
+ * indexed by replica j (not slot) and site i, 1 iff s = -1.  Import recomputes the
+ * energies. */
+sg_status sg_export_spins(sg_handle *h, uint8_t *spins_out, uintptr_t stream);
+sg_status sg_import_spins(sg_handle *h, const uint8_t *spins_in, uintptr_t stream);
+
+/* Couplings, DEVICE buffers: int8 [n_samples][N][ndim], +-1, entry (i, mu) is the bond
+ * from i to i + e_mu.  Import recomputes the energies. */
+sg_status sg_export_couplings(sg_handle *h, int8_t *J_out, uintptr_t stream);
+sg_status sg_import_couplings(sg_handle *h, const int8_t *J_in, uintptr_t stream);
+
+/* Replica state into HOST buffers; synchronises `stream`.  Any pointer may be NULL.
+ *   E_out     [n_samples][n_chains][n_temps]  energy of replica j (Eq. 1)
+ *   perm_out  [n_samples][n_chains][n_temps]  replica at temperature slot k
+ *   steps_out [3]                             t_metro, t_pt, t_houd */
+sg_status sg_get_state(sg_handle *h, int32_t *E_out, int32_t *perm_out, uint64_t *steps_out,
+                       uintptr_t stream);
+
+/* Counters into HOST buffers; synchronises `stream`.  Any pointer may be NULL.
+ *   near_threshold  exchange decisions with |u 2^-32 - exp(delta)| < 1e-12 (expected 0)
+ *   pt_accepts      [n_temps-1] accepted exchanges per pair (k, k+1), summed over chains
+ *   houdayer_sites  total sites flipped by Houdayer moves (each pair counts once) */
+sg_status sg_counters(sg_handle *h, uint64_t *near_threshold, uint64_t *pt_accepts,
+                      uint64_t *houdayer_sites, uintptr_t stream);
+
+/* Metropolis thresholds thr[k][m-1] = min(floor(exp(-4 m beta_k) 2^32), 2^32 - 1),
+ * m = 1..ndim, computed on the host in fp64 (HOST buffer [n_temps][ndim]). */
+sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out);
+
+/* Free the host-side handle.  The caller frees the device buffer afterwards. */
+void sg_destroy(sg_handle *h);
+
+/* Static description of a status code. */
+const char *sg_strerror(sg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGMC_H */

@@ -1,0 +1,443 @@
+// sgmc_api.cu -- host side of the C-ABI declared in include/sgmc.h: parameter checks,
+// the device-memory layout inside the caller's buffer, the host-computed tables
+// (Metropolis thresholds, inverse temperatures) and the kernel launches.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sgmc.h"
+#include "sgmc_internal.cuh"
+
+using namespace sgmc;
+
+namespace {
+
+struct Layout {
+  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+constexpr int MAX_TEMPS = 4096;
+constexpr long long MAX_SITES = 1ll << 26;
+
+} // namespace
+
+struct sg_handle {
+  sg_params p;
+  std::vector<double> temps, beta;
+  std::vector<uint32_t> thr; // [T][4]
+  Job job;
+  Dev dev;
+  Layout lay;
+  char *buf;
+  size_t bytes;
+  uint64_t t_metro, t_pt, t_houd;
+  sg_status sticky;
+  int int8fmt;
+  int nt;          // threads of the resident kernel
+  size_t smem;     // its dynamic shared memory
+  bool fuse_pt;    // the exchange can run inside the resident kernel
+  int n_ctr;       // counters in the device array
+};
+
+namespace {
+
+sg_status validate(const sg_params *p) {
+  if (!p) return SG_EINVAL;
+  if (p->ndim != 2 && p->ndim != 3) return SG_EINVAL;
+  long long N = 1;
+  for (int a = 0; a < p->ndim; ++a) {
+    if (p->dims[a] < 2) return SG_EINVAL;
+    N *= p->dims[a];
+    if (N > MAX_SITES) return SG_EUNSUPPORTED;
+  }
+  if (p->n_samples < 1 || p->sample_offset < 0) return SG_EINVAL;
+  if (p->n_chains != 1 && p->n_chains != 2) return SG_EINVAL;
+  if (p->n_temps < 1 || p->n_temps > MAX_TEMPS || !p->temps) return SG_EINVAL;
+  for (int k = 0; k < p->n_temps; ++k) {
+    if (!(p->temps[k] > 0.0) || !std::isfinite(p->temps[k])) return SG_EINVAL;
+    if (k > 0 && !(p->temps[k] > p->temps[k - 1])) return SG_EINVAL;
+  }
+  if (!(p->p_plus >= 0.0 && p->p_plus <= 1.0)) return SG_EINVAL;
+  if (p->spin_format != SG_PACKED32 && p->spin_format != SG_INT8) return SG_EINVAL;
+  if (p->houdayer != 0 && p->houdayer != 1) return SG_EINVAL;
+  if (p->houdayer && p->n_chains != 2) return SG_EINVAL;
+  if (p->n_metro < 1 || p->reserved != 0) return SG_EINVAL;
+  for (int a = 0; a < p->ndim; ++a)
+    if (p->dims[a] % 2) return SG_EUNSUPPORTED; // checkerboard needs even extents
+  return SG_OK;
+}
+
+void build_job(const sg_params *p, Job *jb) {
+  Geo &g = jb->g;
+  g.d = p->ndim;
+  g.L0 = p->dims[0];
+  g.L1 = p->dims[1];
+  g.L2 = p->ndim == 3 ? p->dims[2] : 1;
+  g.N = g.L0 * g.L1 * g.L2;
+  g.H = g.L0 / 2;
+  g.R = g.L1 * g.L2;
+  g.Nh = g.N / 2;
+  g.NW = (((g.N + 31) / 32) + 3) & ~3; // multiple of 4 words: 16-byte aligned planes
+  jb->S = p->n_samples;
+  jb->s_off = p->sample_offset;
+  jb->C = p->n_chains;
+  jb->T = p->n_temps;
+  jb->Wc = (p->n_temps + 31) / 32;
+  jb->W = jb->C * jb->Wc;
+  jb->Tp = (p->n_temps + 3) & ~3;
+  jb->sk0 = (uint32_t)(p->sim_seed & 0xFFFFFFFFu);
+  jb->sk1 = (uint32_t)(p->sim_seed >> 32);
+  jb->ck0 = (uint32_t)(p->coupling_seed & 0xFFFFFFFFu);
+  jb->ck1 = (uint32_t)(p->coupling_seed >> 32);
+  double cut = std::floor(std::ldexp(p->p_plus, 32));
+  if (cut < 0.0) cut = 0.0;
+  if (cut > 4294967296.0) cut = 4294967296.0;
+  jb->jcut = (unsigned long long)cut;
+}
+
+Layout layout_of(const sg_params *p, const Job &jb) {
+  const Geo &g = jb.g;
+  const size_t S = (size_t)jb.S, C = (size_t)jb.C, T = (size_t)jb.T, N = (size_t)g.N;
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const size_t spin_bytes = p->spin_format == SG_INT8 ? S * C * N * (size_t)jb.Tp : S * (size_t)jb.W * N * 4;
+  L.spins = take(spin_bytes);
+  L.jbits = take(S * (size_t)g.d * (size_t)g.NW * 4);
+  L.E = take(S * C * T * 4);
+  L.perm = take(S * C * T * 4);
+  L.slot = take(S * C * T * 4);
+  L.thr = take(T * 4 * 4);
+  L.beta = take(T * 8);
+  L.ctr = take((size_t)(CTR_PT + T) * 8);
+  L.meas_E = take(S * C * T * 4);
+  L.meas_Q = take(S * T * 4);
+  L.total = off;
+  return L;
+}
+
+uint32_t metropolis_threshold(double beta, int dE) {
+  const double v = std::floor(std::ldexp(std::exp(-(beta * (double)dE)), 32));
+  return v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
+int max_dyn_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  return v;
+}
+
+// Choose the resident kernel's CTA size: the smallest of 256/512/1024 threads whose
+// per-thread colour-1 sites keep the 8-plane vertical counter below 256.
+bool choose_resident(sg_handle *h, int smem_limit) {
+  const Geo &g = h->job.g;
+  if (h->int8fmt) {
+    const Int8Smem L = int8_smem(g.N, g.NW, g.d, h->job.T, h->job.Tp);
+    h->nt = 256;
+    h->smem = (size_t)L.total;
+    return L.total <= smem_limit;
+  }
+  for (int nt : {256, 512, 1024}) {
+    const int per_thread = (g.Nh + nt - 1) / nt;
+    if (per_thread * 2 * g.d > 255) continue;
+    const PackedSmem L = packed_smem(g.N, g.NW, g.d, nt);
+    if (L.total > smem_limit) return false;
+    h->nt = nt;
+    h->smem = (size_t)L.total;
+    return true;
+  }
+  return false;
+}
+
+sg_status check(sg_handle *h, cudaError_t e) {
+  if (e != cudaSuccess) {
+    h->sticky = SG_ECUDA;
+    return SG_ECUDA;
+  }
+  return SG_OK;
+}
+
+template <bool FUSE, bool EONLY>
+sg_status launch_resident(sg_handle *h, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0, int n_mcs,
+                          int n_metro) {
+  return check(h, sgmc::launch_resident(h->job, h->dev, h->int8fmt != 0, h->nt, FUSE, EONLY, h->smem, st,
+                                        t_metro0, t_pt0, n_mcs, n_metro));
+}
+
+cudaStream_t as_stream(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+sg_status sweeps(sg_handle *h, int n, cudaStream_t st) {
+  if (n <= 0) return SG_OK;
+  sg_status r = launch_resident<false, false>(h, st, (uint32_t)h->t_metro, 0u, n, 1);
+  if (r == SG_OK) h->t_metro += (uint64_t)n;
+  return r;
+}
+
+sg_status exchange(sg_handle *h, cudaStream_t st) {
+  sg_status r = check(h, launch_exchange(h->job, h->dev, (uint32_t)h->t_pt, st));
+  if (r == SG_OK) h->t_pt += 1;
+  return r;
+}
+
+sg_status recompute_energy(sg_handle *h, cudaStream_t st) {
+  return launch_resident<false, true>(h, st, 0u, 0u, 1, 1);
+}
+
+// Read the device error word; poison the handle if a bounded wait expired.
+sg_status poll_device_error(sg_handle *h, cudaStream_t st) {
+  unsigned long long err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, h->dev.ctr + CTR_ERROR, sizeof(err), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return check(h, e);
+  if (err) {
+    h->sticky = SG_ETIMEOUT;
+    return SG_ETIMEOUT;
+  }
+  return SG_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+sg_status sg_query_bytes(const sg_params *p, size_t *device_bytes) {
+  if (!device_bytes) return SG_EINVAL;
+  const sg_status v = validate(p);
+  if (v != SG_OK) return v;
+  Job jb;
+  build_job(p, &jb);
+  *device_bytes = layout_of(p, jb).total;
+  return SG_OK;
+}
+
+sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_t stream, sg_handle **out) {
+  if (!out) return SG_EINVAL;
+  *out = nullptr;
+  const sg_status v = validate(p);
+  if (v != SG_OK) return v;
+  if (!device_buf || (reinterpret_cast<uintptr_t>(device_buf) & 255u)) return SG_EINVAL;
+  sg_handle *h = new (std::nothrow) sg_handle();
+  if (!h) return SG_ENOMEM;
+  h->p = *p;
+  h->temps.assign(p->temps, p->temps + p->n_temps);
+  h->p.temps = nullptr;
+  build_job(p, &h->job);
+  h->lay = layout_of(p, h->job);
+  if (bytes < h->lay.total) {
+    delete h;
+    return SG_ENOMEM;
+  }
+  h->buf = static_cast<char *>(device_buf);
+  h->bytes = bytes;
+  h->t_metro = h->t_pt = h->t_houd = 0;
+  h->sticky = SG_OK;
+  h->int8fmt = p->spin_format == SG_INT8;
+  const int T = p->n_temps, d = p->ndim;
+  if (!choose_resident(h, max_dyn_smem())) {
+    delete h;
+    return SG_EUNSUPPORTED;
+  }
+  h->fuse_pt = h->int8fmt ? true : (h->job.Wc == 1);
+  h->n_ctr = CTR_PT + T;
+
+  h->beta.resize(T);
+  h->thr.assign((size_t)T * 4, 0u);
+  for (int k = 0; k < T; ++k) {
+    h->beta[k] = 1.0 / h->temps[k];
+    for (int m = 1; m <= d; ++m) h->thr[(size_t)k * 4 + m] = metropolis_threshold(h->beta[k], 4 * m);
+  }
+  Dev &dv = h->dev;
+  dv.spins = reinterpret_cast<uint32_t *>(h->buf + h->lay.spins);
+  dv.jbits = reinterpret_cast<uint32_t *>(h->buf + h->lay.jbits);
+  dv.E = reinterpret_cast<int32_t *>(h->buf + h->lay.E);
+  dv.perm = reinterpret_cast<int32_t *>(h->buf + h->lay.perm);
+  dv.slot = reinterpret_cast<int32_t *>(h->buf + h->lay.slot);
+  dv.thr = reinterpret_cast<const uint32_t *>(h->buf + h->lay.thr);
+  dv.beta = reinterpret_cast<const double *>(h->buf + h->lay.beta);
+  dv.ctr = reinterpret_cast<unsigned long long *>(h->buf + h->lay.ctr);
+
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(h->buf + h->lay.thr, h->thr.data(), h->thr.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->buf + h->lay.beta, h->beta.data(), h->beta.size() * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dv.ctr, 0, (size_t)h->n_ctr * 8, st);
+  if (e == cudaSuccess) e = launch_init(h->job, dv, h->int8fmt != 0, st);
+  if (e != cudaSuccess) {
+    delete h;
+    return SG_ECUDA;
+  }
+  if (recompute_energy(h, st) != SG_OK) {
+    delete h;
+    return SG_ECUDA;
+  }
+  // the pageable host tables above must not be freed before the copies have read them
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    delete h;
+    return SG_ECUDA;
+  }
+  *out = h;
+  return SG_OK;
+}
+
+sg_status sg_sweep(sg_handle *h, int32_t n_sweeps, uintptr_t stream) {
+  if (!h || n_sweeps < 0) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  return sweeps(h, n_sweeps, as_stream(stream));
+}
+
+sg_status sg_exchange(sg_handle *h, uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  return exchange(h, as_stream(stream));
+}
+
+sg_status sg_houdayer(sg_handle *h, uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  (void)stream;
+  if (h->job.C != 2) return SG_EINVAL;
+  return SG_EUNSUPPORTED;
+}
+
+sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
+  if (!h || n_mcs < 0) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (n_mcs == 0) return SG_OK;
+  cudaStream_t st = as_stream(stream);
+  const int nm = h->p.n_metro;
+  if (!h->p.houdayer && h->fuse_pt) {
+    sg_status r = launch_resident<true, false>(h, st, (uint32_t)h->t_metro, (uint32_t)h->t_pt, n_mcs, nm);
+    if (r == SG_OK) {
+      h->t_metro += (uint64_t)n_mcs * (uint64_t)nm;
+      h->t_pt += (uint64_t)n_mcs;
+    }
+    return r;
+  }
+  for (int m = 0; m < n_mcs; ++m) {
+    sg_status r = sweeps(h, nm, st);
+    if (r == SG_OK && h->p.houdayer) r = sg_houdayer(h, stream);
+    if (r == SG_OK) r = exchange(h, st);
+    if (r != SG_OK) return r;
+  }
+  return SG_OK;
+}
+
+sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
+  if (!h || !E_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  return check(h, launch_measure(h->job, h->dev, h->int8fmt != 0, E_out, Q_out, st));
+}
+
+sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
+  if (!h || !E_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  int32_t *dE = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_E);
+  int32_t *dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q);
+  const bool want_q = Q_out && h->job.C >= 2;
+  sg_status r = sg_measure_device(h, dE, want_q ? dQ : nullptr, stream);
+  if (r != SG_OK) return r;
+  const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
+  cudaError_t e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  return poll_device_error(h, st);
+}
+
+sg_status sg_export_spins(sg_handle *h, uint8_t *spins_out, uintptr_t stream) {
+  if (!h || !spins_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  return check(h, launch_export_spins(h->job, h->dev, h->int8fmt != 0, spins_out, as_stream(stream)));
+}
+
+sg_status sg_import_spins(sg_handle *h, const uint8_t *spins_in, uintptr_t stream) {
+  if (!h || !spins_in) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  sg_status r = check(h, launch_import_spins(h->job, h->dev, h->int8fmt != 0, spins_in, st));
+  return r == SG_OK ? recompute_energy(h, st) : r;
+}
+
+sg_status sg_export_couplings(sg_handle *h, int8_t *J_out, uintptr_t stream) {
+  if (!h || !J_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  return check(h, launch_export_couplings(h->job, h->dev, J_out, as_stream(stream)));
+}
+
+sg_status sg_import_couplings(sg_handle *h, const int8_t *J_in, uintptr_t stream) {
+  if (!h || !J_in) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  sg_status r = check(h, launch_import_couplings(h->job, h->dev, J_in, st));
+  return r == SG_OK ? recompute_energy(h, st) : r;
+}
+
+sg_status sg_get_state(sg_handle *h, int32_t *E_out, int32_t *perm_out, uint64_t *steps_out, uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  const size_t n = (size_t)h->job.S * h->job.C * h->job.T;
+  cudaError_t e = cudaSuccess;
+  if (E_out) e = cudaMemcpyAsync(E_out, h->dev.E, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && perm_out) e = cudaMemcpyAsync(perm_out, h->dev.perm, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  if (steps_out) {
+    steps_out[0] = h->t_metro;
+    steps_out[1] = h->t_pt;
+    steps_out[2] = h->t_houd;
+  }
+  return poll_device_error(h, st);
+}
+
+sg_status sg_counters(sg_handle *h, uint64_t *near_threshold, uint64_t *pt_accepts, uint64_t *houdayer_sites,
+                      uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  std::vector<unsigned long long> c((size_t)h->n_ctr);
+  cudaError_t e = cudaMemcpyAsync(c.data(), h->dev.ctr, c.size() * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return check(h, e);
+  if (c[CTR_ERROR]) {
+    h->sticky = SG_ETIMEOUT;
+    return SG_ETIMEOUT;
+  }
+  if (near_threshold) *near_threshold = c[CTR_NEAR];
+  if (houdayer_sites) *houdayer_sites = c[CTR_HSITES];
+  if (pt_accepts)
+    for (int k = 0; k + 1 < h->job.T; ++k) pt_accepts[k] = c[CTR_PT + k];
+  return SG_OK;
+}
+
+sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out) {
+  if (!h || !thr_out) return SG_EINVAL;
+  const int d = h->job.g.d;
+  for (int k = 0; k < h->job.T; ++k)
+    for (int m = 1; m <= d; ++m) thr_out[k * d + (m - 1)] = h->thr[(size_t)k * 4 + m];
+  return SG_OK;
+}
+
+void sg_destroy(sg_handle *h) { delete h; }
+
+const char *sg_strerror(sg_status s) {
+  switch (s) {
+  case SG_OK: return "ok";
+  case SG_EINVAL: return "invalid argument";
+  case SG_ENOMEM: return "device buffer too small";
+  case SG_ECUDA: return "CUDA error";
+  case SG_ETIMEOUT: return "bounded device wait expired";
+  case SG_EUNSUPPORTED: return "unsupported parameters";
+  }
+  return "unknown status";
+}
+
+} // extern "C"

@@ -1,0 +1,249 @@
+// sgmc_internal.cuh -- device-side definitions shared by the engine's kernels.
+//
+// Data layout in HBM (all inside the caller's buffer, each array 256-byte aligned):
+//   spins, packed   uint32 [S][W][N]      W = C * Wc words per site, Wc = ceil(T/32);
+//                                         word w holds chain c = w / Wc, replicas
+//                                         j = 32 (w % Wc) + lane, lane = bit
+//   spins, int8     int8   [S][C][N][Tp]  +-1, Tp = T rounded up to 4
+//   couplings       uint32 [S][d][NW]     one bit plane per axis mu, bit p of plane mu is
+//                                         1 iff J(i(p), mu) = -1; NW = ceil(N/32)
+//   E, perm, slot   int32  [S][C][T]      energy of replica j; replica at slot k; slot of j
+//   thr             uint32 [T][4]         thr[k][m] for m = 1..d (entry 0 unused)
+//   beta            double [T]
+//   counters        u64    [CTR_PT + T]   see CTR_* below
+// Sites are stored in colour-split order p: the N/2 colour-0 sites first, then the
+// colour-1 sites; inside a colour, row = y + L1 z and half-column k = x / 2, so
+// p = c N/2 + row H + k with H = L0 / 2, and x = 2k + (c ^ ((y + z) & 1)).  A
+// colour's neighbours are all in the other colour's half, at the same k (or k +- 1
+// along x) of the neighbouring rows, so a half-sweep reads both halves contiguously.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sgmc {
+
+// Philox stream tags (the last counter word's low byte).
+constexpr uint32_t TAG_METRO = 0u, TAG_PT = 1u, TAG_HOUD = 2u, TAG_INIT = 3u, TAG_J = 4u;
+
+// Counter slots in the device counter array.
+constexpr int CTR_NEAR = 0;   // near-threshold exchange decisions
+constexpr int CTR_HSITES = 1; // sites flipped by Houdayer moves
+constexpr int CTR_ERROR = 2;  // bit flags of device-side errors (bounded waits that expired)
+constexpr int CTR_HMOVES = 3; // Houdayer moves with M > 0
+constexpr int CTR_PT = 4;     // [T-1] accepted exchanges per pair
+
+constexpr unsigned long long ERR_TMA_TIMEOUT = 1ull;
+
+struct Geo {
+  int d;          // 2 or 3
+  int L0, L1, L2; // L2 = 1 in 2D
+  int N;          // sites
+  int H;          // L0 / 2
+  int R;          // rows, L1 * L2
+  int Nh;         // N / 2
+  int NW;         // 32-bit words per coupling bit plane
+};
+
+struct Job {
+  Geo g;
+  int S, s_off, C, T, Wc, W, Tp;
+  uint32_t sk0, sk1;       // sim_seed as a Philox key
+  uint32_t ck0, ck1;       // coupling_seed as a Philox key
+  unsigned long long jcut; // J = +1 iff the word is below this (floor(p 2^32), up to 2^32)
+};
+
+struct Dev {
+  uint32_t *spins;
+  uint32_t *jbits;
+  int32_t *E;
+  int32_t *perm;
+  int32_t *slot;
+  const uint32_t *thr;
+  const double *beta;
+  unsigned long long *ctr;
+};
+
+// ---------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies; the new state is (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0); the key is
+// bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------------
+constexpr uint32_t PH_M0 = 0xD2511F53u, PH_M1 = 0xCD9E8D57u;
+constexpr uint32_t PH_W0 = 0x9E3779B9u, PH_W1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox10(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                          uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(PH_M0, x0), lo0 = PH_M0 * x0;
+    const uint32_t hi1 = __umulhi(PH_M1, x2), lo1 = PH_M1 * x2;
+    const uint32_t y0 = hi1 ^ x1 ^ k0;
+    const uint32_t y2 = hi0 ^ x3 ^ k1;
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
+    k0 += PH_W0;
+    k1 += PH_W1;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+// ---------------------------------------------------------------------------------
+// Geometry helpers (colour-split order)
+// ---------------------------------------------------------------------------------
+struct SiteGeo {
+  int c, row, k, y, z, xodd;
+};
+
+__device__ __forceinline__ SiteGeo site_geo(const Geo &g, int p) {
+  SiteGeo s;
+  s.c = p >= g.Nh;
+  const int q = p - s.c * g.Nh;
+  s.row = q / g.H;
+  s.k = q - s.row * g.H;
+  s.y = s.row % g.L1;
+  s.z = s.row / g.L1;
+  s.xodd = s.c ^ ((s.y + s.z) & 1);
+  return s;
+}
+
+// canonical site index i = x + L0 (y + L1 z)
+__device__ __forceinline__ int canonical_of(const Geo &g, const SiteGeo &s) {
+  return g.L0 * s.row + 2 * s.k + s.xodd;
+}
+
+__device__ __forceinline__ int cs_of_canonical(const Geo &g, int i) {
+  const int x = i % g.L0;
+  const int row = i / g.L0;
+  const int y = row % g.L1;
+  const int z = row / g.L1;
+  const int c = (x + y + z) & 1;
+  return c * g.Nh + row * g.H + (x >> 1);
+}
+
+// Colour-split index of the neighbour of site s one step along axis mu (dir = +1/-1).
+__device__ __forceinline__ int nbr_cs(const Geo &g, const SiteGeo &s, int mu, int dir) {
+  const int base = (1 - s.c) * g.Nh;
+  if (mu == 0) {
+    int k2;
+    if (dir > 0) k2 = s.xodd ? (s.k + 1 == g.H ? 0 : s.k + 1) : s.k;
+    else k2 = s.xodd ? s.k : (s.k == 0 ? g.H - 1 : s.k - 1);
+    return base + s.row * g.H + k2;
+  }
+  if (mu == 1) {
+    int y2 = s.y + dir;
+    y2 = y2 < 0 ? g.L1 - 1 : (y2 == g.L1 ? 0 : y2);
+    return base + (y2 + g.L1 * s.z) * g.H + s.k;
+  }
+  int z2 = s.z + dir;
+  z2 = z2 < 0 ? g.L2 - 1 : (z2 == g.L2 ? 0 : z2);
+  return base + (s.y + g.L1 * z2) * g.H + s.k;
+}
+
+// Bit-sliced full adder: sum and carry of three 32-lane bit planes.
+__device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy) {
+  s = a ^ b ^ c;
+  cy = (a & b) | (c & (a ^ b));
+}
+
+// ---------------------------------------------------------------------------------
+// Replica exchange of one chain (Eq. 5), run by ONE thread: for k = 0..T-2 in order,
+// delta = (beta_k - beta_k+1)(E_perm[k] - E_perm[k+1]); accept iff delta >= 0 or
+// u 2^-32 < exp(delta), u the chain's Philox word for (k, t).  perm/slot/E may live in
+// shared or global memory.  on_accept(k) and on_near() report to the caller.  The fp64
+// arithmetic uses explicit round-to-nearest intrinsics so that no contraction can
+// make it differ from the host oracle.
+// ---------------------------------------------------------------------------------
+template <class OnAccept, class OnNear>
+__device__ __forceinline__ void exchange_chain(int T, const double *beta, int32_t *perm, int32_t *slot,
+                                               const int32_t *E, uint32_t s_glob, uint32_t c,
+                                               uint32_t t, uint32_t k0, uint32_t k1, OnAccept on_accept,
+                                               OnNear on_near) {
+  for (int k = 0; k + 1 < T; ++k) {
+    const int a = perm[k], b = perm[k + 1];
+    const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
+    const double delta = __dmul_rn(dbeta, (double)(E[a] - E[b]));
+    bool accept;
+    if (delta >= 0.0) {
+      accept = true;
+    } else {
+      const uint32_t u = philox10((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, k0, k1).x;
+      const double x = __dmul_rn((double)u, 0x1p-32);
+      const double e = exp(delta);
+      if (fabs(__dsub_rn(x, e)) < 1e-12) on_near();
+      accept = x < e;
+    }
+    if (accept) {
+      on_accept(k);
+      perm[k] = b;
+      perm[k + 1] = a;
+      slot[a] = k + 1;
+      slot[b] = k;
+    }
+  }
+}
+
+} // namespace sgmc
+
+namespace sgmc {
+
+__host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
+
+// Shared-memory map of the resident packed kernel (one 32-replica word lattice).
+struct PackedSmem {
+  int spin, jbyte, jpl, thr, epart, pt, bar, total;
+};
+__host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthreads) {
+  PackedSmem L;
+  L.spin = 0;
+  L.jbyte = L.spin + 4 * N;
+  L.jpl = L.jbyte + round16(N);
+  L.thr = L.jpl + round16(4 * d * NW);
+  L.epart = L.thr + 32 * 4 * 4;
+  L.pt = L.epart + 4 * nthreads;
+  L.bar = L.pt + round16(4 * 32 * 4 + 16);
+  L.total = L.bar + 16;
+  return L;
+}
+
+// Shared-memory map of the resident int8 kernel (one chain, all its replicas).
+struct Int8Smem {
+  int spin, jbyte, jpl, thr, eacc, pm, sl, pacc, near, bar, total;
+};
+__host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int Tp) {
+  Int8Smem L;
+  L.spin = 0;
+  L.jbyte = L.spin + round16(N * Tp);
+  L.jpl = L.jbyte + round16(N);
+  L.thr = L.jpl + round16(4 * d * NW);
+  L.eacc = L.thr + 16 * Tp;
+  L.pm = L.eacc + round16(4 * Tp);
+  L.sl = L.pm + round16(4 * T);
+  L.pacc = L.sl + round16(4 * T);
+  L.near = L.pacc + round16(4 * T);
+  L.bar = L.near + 16;
+  L.total = L.bar + 16;
+  return L;
+}
+
+// Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
+cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, bool fuse_pt,
+                            bool energy_only, size_t smem, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0,
+                            int n_mcs, int n_metro);
+cudaError_t launch_exchange(const Job &jb, const Dev &dv, uint32_t t_pt, cudaStream_t st);
+} // namespace sgmc
+
+namespace sgmc {
+cudaError_t launch_init(const Job &jb, const Dev &dv, bool int8fmt, cudaStream_t st);
+cudaError_t launch_export_spins(const Job &jb, const Dev &dv, bool int8fmt, uint8_t *out, cudaStream_t st);
+cudaError_t launch_import_spins(const Job &jb, const Dev &dv, bool int8fmt, const uint8_t *in, cudaStream_t st);
+cudaError_t launch_export_couplings(const Job &jb, const Dev &dv, int8_t *out, cudaStream_t st);
+cudaError_t launch_import_couplings(const Job &jb, const Dev &dv, const int8_t *in, cudaStream_t st);
+cudaError_t launch_measure(const Job &jb, const Dev &dv, bool int8fmt, int32_t *E_out, int32_t *Q_out,
+                           cudaStream_t st);
+} // namespace sgmc

@@ -1,0 +1,274 @@
+"""Python binding of the engine's C-ABI (``include/sgmc.h``, ``libsgmc.so``).
+
+Argument marshalling only: every step of the simulation runs in the library's CUDA
+kernels.  PyTorch supplies the device buffer the handle lives in and the CUDA stream
+its work is queued on.  There is no CPU fallback: if the library is not built, or no
+CUDA device is present, constructing a Simulation raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgmc.so")
+
+SG_PACKED32 = 0
+SG_INT8 = 1
+
+STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETIMEOUT", 5: "SG_EUNSUPPORTED"}
+
+
+class SGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32),
+        ("dims", ctypes.c_int32 * 3),
+        ("n_samples", ctypes.c_int32),
+        ("sample_offset", ctypes.c_int32),
+        ("n_chains", ctypes.c_int32),
+        ("n_temps", ctypes.c_int32),
+        ("temps", ctypes.POINTER(ctypes.c_double)),
+        ("coupling_seed", ctypes.c_uint64),
+        ("p_plus", ctypes.c_double),
+        ("sim_seed", ctypes.c_uint64),
+        ("spin_format", ctypes.c_int32),
+        ("houdayer", ctypes.c_int32),
+        ("n_metro", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+EXPORTED = (
+    "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_run_mcs", "sg_measure",
+    "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_get_state", "sg_counters", "sg_thresholds", "sg_destroy", "sg_strerror",
+)
+
+_lib = None
+
+
+def lib():
+    """Load ``libsgmc.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_2003_04621_gb300.build.build() (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    # uintptr_t stream handles are 64-bit on every supported platform
+    P, U, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t
+    PP = ctypes.POINTER(Params)
+    sig = {
+        "sg_query_bytes": [PP, ctypes.POINTER(SZ)],
+        "sg_create": [PP, P, SZ, U, ctypes.POINTER(P)],
+        "sg_sweep": [P, I32, U],
+        "sg_exchange": [P, U],
+        "sg_houdayer": [P, U],
+        "sg_run_mcs": [P, I32, U],
+        "sg_measure": [P, P, P, U],
+        "sg_measure_device": [P, P, P, U],
+        "sg_export_spins": [P, P, U],
+        "sg_import_spins": [P, P, U],
+        "sg_export_couplings": [P, P, U],
+        "sg_import_couplings": [P, P, U],
+        "sg_get_state": [P, P, P, P, U],
+        "sg_counters": [P, P, P, P, U],
+        "sg_thresholds": [P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.sg_destroy.argtypes = [P]
+    L.sg_destroy.restype = None
+    L.sg_strerror.argtypes = [ctypes.c_int]
+    L.sg_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SGError(status, where)
+
+
+def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, temps: Sequence[float],
+                coupling_seed: int = 1, sim_seed: int = 1, p_plus: float = 0.5, spin_format: str = "packed",
+                houdayer: bool = False, n_metro: int = 1, sample_offset: int = 0):
+    """Fill an sg_params; returns (params, temps_array) -- keep the array alive."""
+    t = np.ascontiguousarray(np.asarray(temps, dtype=np.float64))
+    p = Params()
+    p.ndim = int(ndim)
+    for a in range(3):
+        p.dims[a] = int(dims[a]) if a < ndim else 1
+    p.n_samples = int(n_samples)
+    p.sample_offset = int(sample_offset)
+    p.n_chains = int(n_chains)
+    p.n_temps = len(t)
+    p.temps = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.coupling_seed = int(coupling_seed)
+    p.p_plus = float(p_plus)
+    p.sim_seed = int(sim_seed)
+    p.spin_format = SG_INT8 if spin_format == "int8" else SG_PACKED32
+    p.houdayer = int(bool(houdayer))
+    p.n_metro = int(n_metro)
+    p.reserved = 0
+    return p, t
+
+
+def query_bytes(params: Params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().sg_query_bytes(ctypes.byref(params), ctypes.byref(n)), "sg_query_bytes")
+    return int(n.value)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Simulation:
+    """One simulation job on the current CUDA device (see ``include/sgmc.h``)."""
+
+    def __init__(self, ndim, dims, n_samples, n_chains, temps, coupling_seed=1, sim_seed=1, p_plus=0.5,
+                 spin_format="packed", houdayer=False, n_metro=1, sample_offset=0, stream=None, device=None):
+        import torch
+
+        L = lib()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the engine has no CPU path")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.ndim, self.dims = int(ndim), tuple(int(x) for x in dims)[: int(ndim)]
+        self.N = int(np.prod(self.dims))
+        self.S, self.C, self.T = int(n_samples), int(n_chains), len(temps)
+        self.params, self._temps = make_params(ndim, dims, n_samples, n_chains, temps, coupling_seed, sim_seed,
+                                               p_plus, spin_format, houdayer, n_metro, sample_offset)
+        self.bytes = query_bytes(self.params)
+        # 256-byte alignment: over-allocate and offset (torch's allocator aligns further anyway)
+        self._buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._buf.data_ptr()
+        self._ptr = (base + 255) & ~255
+        self._stream = stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.sg_create(ctypes.byref(self.params), ctypes.c_void_p(self._ptr), self.bytes,
+                               _stream_handle(stream), ctypes.byref(h)), "sg_create")
+        self._h = h
+
+    # -- lifetime -------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _s(self, stream=None):
+        return _stream_handle(stream if stream is not None else self._stream)
+
+    # -- dynamics -------------------------------------------------------------------
+    def sweep(self, n: int = 1, stream=None):
+        _check(lib().sg_sweep(self._h, int(n), self._s(stream)), "sg_sweep")
+
+    def exchange(self, stream=None):
+        _check(lib().sg_exchange(self._h, self._s(stream)), "sg_exchange")
+
+    def houdayer(self, stream=None):
+        _check(lib().sg_houdayer(self._h, self._s(stream)), "sg_houdayer")
+
+    def run_mcs(self, n: int = 1, stream=None):
+        _check(lib().sg_run_mcs(self._h, int(n), self._s(stream)), "sg_run_mcs")
+
+    # -- observables and state --------------------------------------------------------
+    def measure(self, stream=None):
+        """(E by slot [S][C][T], N q [S][T] or None) as numpy arrays; synchronises."""
+        E = np.zeros((self.S, self.C, self.T), np.int32)
+        Q = np.zeros((self.S, self.T), np.int32) if self.C >= 2 else None
+        _check(lib().sg_measure(self._h, E.ctypes.data, Q.ctypes.data if Q is not None else None, self._s(stream)),
+               "sg_measure")
+        return E, Q
+
+    def measure_device(self, E_out, Q_out=None, stream=None):
+        """As measure, into torch int32 device tensors; does not synchronise."""
+        _check(lib().sg_measure_device(self._h, E_out.data_ptr(), Q_out.data_ptr() if Q_out is not None else None,
+                                       self._s(stream)), "sg_measure_device")
+
+    def spins(self, stream=None):
+        """uint8 device tensor [S][C][T][N], 1 iff the spin is -1 (replica order)."""
+        import torch
+
+        out = torch.empty((self.S, self.C, self.T, self.N), dtype=torch.uint8, device=self.device)
+        _check(lib().sg_export_spins(self._h, out.data_ptr(), self._s(stream)), "sg_export_spins")
+        return out
+
+    def set_spins(self, bits, stream=None):
+        import torch
+
+        t = torch.as_tensor(np.asarray(bits, dtype=np.uint8) if not torch.is_tensor(bits) else bits)
+        t = t.to(device=self.device, dtype=torch.uint8).contiguous().reshape(self.S, self.C, self.T, self.N)
+        _check(lib().sg_import_spins(self._h, t.data_ptr(), self._s(stream)), "sg_import_spins")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def couplings(self, stream=None):
+        """int8 device tensor [S][N][d] of +-1 couplings."""
+        import torch
+
+        out = torch.empty((self.S, self.N, self.ndim), dtype=torch.int8, device=self.device)
+        _check(lib().sg_export_couplings(self._h, out.data_ptr(), self._s(stream)), "sg_export_couplings")
+        return out
+
+    def set_couplings(self, J, stream=None):
+        import torch
+
+        t = torch.as_tensor(np.asarray(J, dtype=np.int8) if not torch.is_tensor(J) else J)
+        t = t.to(device=self.device, dtype=torch.int8).contiguous().reshape(self.S, self.N, self.ndim)
+        _check(lib().sg_import_couplings(self._h, t.data_ptr(), self._s(stream)), "sg_import_couplings")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def state(self, stream=None):
+        """(E by replica [S][C][T], perm [S][C][T], steps (t_metro, t_pt, t_houd))."""
+        E = np.zeros((self.S, self.C, self.T), np.int32)
+        perm = np.zeros((self.S, self.C, self.T), np.int32)
+        steps = np.zeros(3, np.uint64)
+        _check(lib().sg_get_state(self._h, E.ctypes.data, perm.ctypes.data, steps.ctypes.data, self._s(stream)),
+               "sg_get_state")
+        return E, perm, tuple(int(x) for x in steps)
+
+    def counters(self, stream=None) -> dict:
+        near = np.zeros(1, np.uint64)
+        acc = np.zeros(max(self.T - 1, 1), np.uint64)
+        hs = np.zeros(1, np.uint64)
+        _check(lib().sg_counters(self._h, near.ctypes.data, acc.ctypes.data, hs.ctypes.data, self._s(stream)),
+               "sg_counters")
+        return {"near_threshold": int(near[0]), "pt_accepts": acc[: self.T - 1].copy(),
+                "houdayer_sites": int(hs[0])}
+
+    def thresholds(self) -> np.ndarray:
+        out = np.zeros((self.T, self.ndim), np.uint32)
+        _check(lib().sg_thresholds(self._h, out.ctypes.data), "sg_thresholds")
+        return out
+
+
+def from_workload(w, stream=None, **overrides) -> Simulation:
+    """Create a Simulation from a ``paper_2003_04621_gb300.inputs.Workload``."""
+    kw = dict(ndim=w.ndim, dims=w.dims, n_samples=w.n_samples, n_chains=w.n_chains, temps=list(w.temps),
+              coupling_seed=w.coupling_seed, sim_seed=w.sim_seed, p_plus=w.p_plus, spin_format=w.spin_format,
+              houdayer=w.houdayer, sample_offset=w.sample_offset)
+    kw.update(overrides)
+    return Simulation(stream=stream, **kw)
