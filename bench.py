@@ -197,6 +197,11 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
 
+    # pick the resident kernel's launch shape on a scratch copy (results do not depend on it)
+    from paper_2003_04621_gb300 import autotune
+
+    tuning = autotune.tune(sim, stream=stream)
+    launch = sim.launch()
     for _ in range(max(args.warmup, 3)):
         sim.run_mcs(1)
     # the packed state (36 MB) fits in L2 (129 MB): flush L2 between timed steps
@@ -236,6 +241,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim2 = Simulation(stream=stream, **kw)
+        sim2.set_launch(launch["threads"], launch["words"])
         for _ in range(args.steps):
             sim2.run_mcs(1, stream=stream)
             E, Q = sim2.measure(stream=stream)
@@ -273,13 +279,14 @@ def main():
         "config": {"workload": w.name, "lattice": "3D L=16 periodic", "samples_per_gpu": w.n_samples,
                    "chains": w.n_chains, "temps": w.T, "temp_range": [0.9, 2.0], "spin_format": "packed32",
                    "step": "one MCS = checkerboard Metropolis sweep + replica exchange, one fused launch",
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"samples x{ws}"},
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"samples x{ws}",
+                   "launch": launch},
         "gpu_launches": args.steps,
         "wall_s": wall,
         "clocks": clk,
         "roofline": {"bound": "alu", "achieved": achieved_tips, "peak": peak_tips, "unit": "Tinstr/s",
                      "frac": achieved_tips / peak_tips, "traffic": traffic,
-                     "kernel": "k_resident_packed<3,256,fused PT>",
+                     "kernel": f"k_resident_packed<3,{launch['threads']},{launch['words']},fused PT>",
                      "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled)",
                      "instr_per_attempt": instr_per_attempt},
         "hbm_effective": {"achieved_gbs": hbm_eff, "peak_gbs": pk["hbm_gbs"], "frac": hbm_eff / pk["hbm_gbs"],

@@ -36,8 +36,8 @@
  *   where s = sample_offset + local sample, c = chain, j = replica within its chain,
  *   k = temperature slot and t_* = the number of such steps made before.
  *
- * Device memory is laid out by the engine inside the caller's buffer (see DESIGN notes
- * in the repository); callers reach state only through the calls below.
+ * Device memory is laid out by the engine inside the caller's buffer; callers reach the
+ * state only through the calls below (the import/export calls use plain layouts).
  */
 #ifndef SGMC_H
 #define SGMC_H
@@ -155,6 +155,17 @@ sg_status sg_counters(sg_handle *h, uint64_t *near_threshold, uint64_t *pt_accep
 /* Metropolis thresholds thr[k][m-1] = min(floor(exp(-4 m beta_k) 2^32), 2^32 - 1),
  * m = 1..ndim, computed on the host in fp64 (HOST buffer [n_temps][ndim]). */
 sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out);
+
+/* Launch shape of the resident sweep kernel (not part of the paper: a tuning knob).
+ *   threads  CTA size: 128, 256, 512 or 1024 (0 keeps the current choice)
+ *   words    32-replica words of one sample held by one CTA: 1 or 2 (0 keeps)
+ * Every accepted choice gives bit-identical results; a shape that does not fit the
+ * lattice (shared memory, per-thread counter range, word count) is refused with
+ * SG_EUNSUPPORTED and the previous shape is kept.  Host-only; no device work. */
+sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words);
+
+/* Current launch shape: threads, words per CTA, dynamic shared memory bytes. */
+sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t *smem_bytes);
 
 /* Free the host-side handle.  The caller frees the device buffer afterwards. */
 void sg_destroy(sg_handle *h);

@@ -22,6 +22,9 @@
 namespace sgmc {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
+#ifndef SGMC_MIN_THREADS
+#define SGMC_MIN_THREADS 768 // resident threads per SM the register budget must allow
+#endif
 constexpr int NB = 8; // bit planes of the per-thread vertical counters (sum <= 255)
 
 // Add the 3-plane value (v0, v1, v2) (weights 1, 2, 4) into the NB-plane counter V.
@@ -70,99 +73,205 @@ __device__ __forceinline__ int32_t warp_lane_sum(const uint32_t (&V)[NB]) {
   return v;
 }
 
-// One checkerboard half-sweep over the colour-`col` sites of a resident word lattice.
-// ACCUM: add each site's post-update unsatisfied count to V.  NOFLIP: count only.
-template <int D, int NT, bool ACCUM, bool NOFLIP>
-__device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__restrict__ sp,
-                                           const uint8_t *__restrict__ jbyte,
-                                           const uint32_t *__restrict__ thr_lane, uint32_t vmask,
-                                           int ngroups, uint32_t t, uint32_t s_glob, uint32_t c3base,
-                                           uint32_t k0, uint32_t k1, uint32_t (&V)[NB]) {
-  const int H = g.H, L1 = g.L1, Nh = g.Nh;
-  uint32_t *own = sp + col * Nh;
-  const uint32_t *oth = sp + (1 - col) * Nh;
-  const uint8_t *jown = jbyte + col * Nh;
-  for (int q = threadIdx.x; q < Nh; q += NT) {
-    const int row = q / H;
-    const int k = q - row * H;
-    int y, z;
-    if (D == 3) {
-      z = row / L1;
-      y = row - z * L1;
-    } else {
-      y = row;
-      z = 0;
-    }
-    const int xodd = col ^ ((y + z) & 1);
-    const int rb = row * H;
-    const int kxp = xodd ? (k + 1 == H ? 0 : k + 1) : k;
-    const int kxm = xodd ? k : (k == 0 ? H - 1 : k - 1);
-    const int ryp = (y + 1 == L1) ? row - (L1 - 1) : row + 1;
-    const int rym = (y == 0) ? row + (L1 - 1) : row - 1;
-    const uint32_t s0 = own[q];
-    const uint32_t jb = jown[q];
-    const uint32_t x0 = s0 ^ oth[rb + kxp] ^ (0u - (jb & 1u));
-    const uint32_t x1 = s0 ^ oth[rb + kxm] ^ (0u - ((jb >> 1) & 1u));
-    const uint32_t x2 = s0 ^ oth[ryp * H + k] ^ (0u - ((jb >> 2) & 1u));
-    const uint32_t x3 = s0 ^ oth[rym * H + k] ^ (0u - ((jb >> 3) & 1u));
-    uint32_t sA, cA, u0, u1, u2, aut;
-    uint32_t sB = 0, cB = 0;
-    fadd(x0, x1, x2, sA, cA);
-    if (D == 3) {
-      const int L2 = g.L2;
-      const int rzp = (z + 1 == L2) ? row - (L2 - 1) * L1 : row + L1;
-      const int rzm = (z == 0) ? row + (L2 - 1) * L1 : row - L1;
-      const uint32_t x4 = s0 ^ oth[rzp * H + k] ^ (0u - ((jb >> 4) & 1u));
-      const uint32_t x5 = s0 ^ oth[rzm * H + k] ^ (0u - ((jb >> 5) & 1u));
-      fadd(x3, x4, x5, sB, cB);
-      u0 = sA ^ sB;
-      const uint32_t tt = sA & sB;
-      fadd(cA, cB, tt, u1, u2);
-      aut = u2 | (u1 & u0); // u >= 3
-    } else {
-      u0 = sA ^ x3;
-      const uint32_t tt = sA & x3;
-      u1 = cA ^ tt;
-      u2 = cA & tt;
-      aut = u1 | u2; // u >= 2
-      sB = x3;       // kept for the post-flip count below
-    }
-    uint32_t F = 0;
-    if (!NOFLIP) {
-      uint32_t acc = aut;
-      const uint32_t i = (uint32_t)(g.L0 * row + 2 * k + xodd);
+// Reject-mask accumulation: rej = 2 rej + [r >= thr].  The carry of r - thr is 1 iff
+// r >= thr (for thr = 0 always), so the Metropolis test r < thr costs one subtract and
+// one add-with-carry, and walking the lanes from high to low leaves lane j's reject bit
+// at bit j.
+__device__ __forceinline__ uint32_t push_reject(uint32_t rej, uint32_t r, uint32_t thr) {
+  uint32_t out;
+  asm("{\n\t.reg .u32 t;\n\tsub.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+      : "=r"(out)
+      : "r"(r), "r"(thr), "r"(rej));
+  return out;
+}
+
+// 32x32 -> 64-bit product as one wide multiply: (hi, lo).
+__device__ __forceinline__ void mulwide(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo) {
+  unsigned long long p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  lo = (uint32_t)p;
+  hi = (uint32_t)(p >> 32);
+}
+
+// Per-sweep part of the site counters' Philox calls.  Every call of a sweep has counter
+// (i, t, s, c3) with s and t fixed, so round 1's product M1 * s and round 2's product
+// M0 * (round-1 word 0) are the same for every site and are computed once.
+struct PhiloxSweep {
+  uint32_t B;        // round 1 output word 1: lo(M1 s)
+  uint32_t hiA, loA; // round 2 product M0 * A, A = hi(M1 s) ^ t ^ k0[0]
+};
+
+__device__ __forceinline__ PhiloxSweep philox_sweep(uint32_t s_glob, uint32_t t, const Job &jb) {
+  PhiloxSweep P;
+  const uint32_t hi1 = __umulhi(PH_M1, s_glob);
+  P.B = PH_M1 * s_glob;
+  const uint32_t A = hi1 ^ t ^ jb.rk0[0];
+  P.hiA = __umulhi(PH_M0, A);
+  P.loA = PH_M0 * A;
+  return P;
+}
+
+// Per-site part: round 1's product M0 * i and round 3's product M1 * (round-2 word 2).
+struct PhiloxSite {
+  uint32_t X;        // hi(M0 i) ^ k1[0]: round-1 word 2 before the counter's c3 is mixed in
+  uint32_t z3;       // round 2 output word 3
+  uint32_t hiZ, loZ; // round 3 product M1 * z2
+};
+
+__device__ __forceinline__ PhiloxSite philox_site(const PhiloxSweep &P, uint32_t i, const Job &jb) {
+  PhiloxSite Q;
+  const uint32_t hi0 = __umulhi(PH_M0, i), lo0 = PH_M0 * i;
+  Q.X = hi0 ^ jb.rk1[0];
+  const uint32_t z2 = P.hiA ^ lo0 ^ jb.rk1[1];
+  Q.z3 = P.loA;
+  Q.hiZ = __umulhi(PH_M1, z2);
+  Q.loZ = PH_M1 * z2;
+  return Q;
+}
+
+// The rest of one Philox4x32-10 call with counter (i, t, s, c3): rounds 2..10.
+__device__ __forceinline__ uint4 philox_finish(const PhiloxSweep &P, const PhiloxSite &Q, uint32_t c3,
+                                               const Job &jb) {
+  const uint32_t y2 = Q.X ^ c3; // round 1 word 2
+  // round 2: products M0 * A (per sweep) and M1 * y2
+  uint32_t r2hi, r2lo;
+  mulwide(PH_M1, y2, r2hi, r2lo);
+  const uint32_t z0 = r2hi ^ P.B ^ jb.rk0[1];
+  const uint32_t z1 = r2lo;
+  // round 3: products M0 * z0 and M1 * z2 (per site)
+  uint32_t p3hi, p3lo;
+  mulwide(PH_M0, z0, p3hi, p3lo);
+  uint32_t x0 = Q.hiZ ^ z1 ^ jb.rk0[2];
+  uint32_t x1 = Q.loZ;
+  uint32_t x2 = p3hi ^ Q.z3 ^ jb.rk1[2];
+  uint32_t x3 = p3lo;
 #pragma unroll
-      for (int gi = 0; gi < 8; ++gi) {
-        if (gi < ngroups) {
-          const uint4 r = philox10(i, t, s_glob, c3base | ((uint32_t)gi << 8), k0, k1);
+  for (int r = 3; r < 10; ++r) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulwide(PH_M0, x0, hi0, lo0);
+    mulwide(PH_M1, x2, hi1, lo1);
+    const uint32_t y0 = hi1 ^ x1 ^ jb.rk0[r];
+    const uint32_t yy2 = hi0 ^ x3 ^ jb.rk1[r];
+    x0 = y0;
+    x1 = lo1;
+    x2 = yy2;
+    x3 = lo0;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+// Bit-sliced unsatisfied-bond count of one site for 32 replicas: the adder planes.
+template <int D>
+struct SiteCount {
+  uint32_t u0, u1, aut;    // u = count (low two bits) and the auto-accept mask (u >= d)
+  uint32_t sA, cA, sB, cB; // adder planes, kept to recount after the flip
+  uint32_t u2;
+};
+
+template <int D>
+__device__ __forceinline__ SiteCount<D> count_site(uint32_t s0, const uint32_t *nb, const uint32_t *jm) {
+  SiteCount<D> r;
+  const uint32_t x0 = s0 ^ nb[0] ^ jm[0];
+  const uint32_t x1 = s0 ^ nb[1] ^ jm[1];
+  const uint32_t x2 = s0 ^ nb[2] ^ jm[2];
+  const uint32_t x3 = s0 ^ nb[3] ^ jm[3];
+  fadd(x0, x1, x2, r.sA, r.cA);
+  if (D == 3) {
+    const uint32_t x4 = s0 ^ nb[4] ^ jm[4];
+    const uint32_t x5 = s0 ^ nb[5] ^ jm[5];
+    fadd(x3, x4, x5, r.sB, r.cB);
+    r.u0 = r.sA ^ r.sB;
+    const uint32_t tt = r.sA & r.sB;
+    fadd(r.cA, r.cB, tt, r.u1, r.u2);
+    r.aut = r.u2 | (r.u1 & r.u0); // u >= 3
+  } else {
+    r.sB = x3;
+    r.cB = 0u;
+    r.u0 = r.sA ^ x3;
+    const uint32_t tt = r.sA & x3;
+    r.u1 = r.cA ^ tt;
+    r.u2 = r.cA & tt;
+    r.aut = r.u1 | r.u2; // u >= 2
+  }
+  return r;
+}
+
+// Post-flip count planes (v1, v2) of the site: flipping s_i toggles all its bonds, so
+// every adder input, sum and carry plane is toggled by F; the low bit is unchanged.
+template <int D>
+__device__ __forceinline__ void recount(const SiteCount<D> &c, uint32_t F, uint32_t &v1, uint32_t &v2) {
+  if (D == 3) {
+    fadd(c.cA ^ F, c.cB ^ F, (c.sA ^ F) & (c.sB ^ F), v1, v2);
+  } else {
+    const uint32_t tt2 = (c.sA ^ F) & (c.sB ^ F);
+    v1 = (c.cA ^ F) ^ tt2;
+    v2 = (c.cA ^ F) & tt2;
+  }
+}
+
+// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.
+// pair_tab holds, for each pair of lanes (2p, 2p+1) and each 4-bit code
+// (u0_2p, u0_2p+1, u1_2p, u1_2p+1), the two lanes' thresholds for their counts u
+// (m = d - u), 8 bytes per entry: one 64-bit load serves two lanes, and the code is
+// cut from the count planes with two shifts and one three-input logic op.
+template <int D>
+__device__ __forceinline__ uint32_t decide_site(const SiteCount<D> &cnt, const PhiloxSweep &P,
+                                                const PhiloxSite &Q, uint32_t c3base, int ngroups,
+                                                const uint2 *__restrict__ pair_tab, const Job &jb) {
+  uint32_t rej = 0;
 #pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            const int j = gi * 4 + qq;
-            uint32_t idx;
-            if (D == 3) idx = ((u0 >> j) & 1u) | (((u1 >> j) & 1u) << 1);
-            else idx = (u0 >> j) & 1u;
-            if (word_of(r, qq) < thr_lane[j * 4 + idx]) acc |= 1u << j;
-          }
-        }
+  for (int gi = 7; gi >= 0; --gi) {
+    if (gi < ngroups) {
+      const uint4 r = philox_finish(P, Q, c3base | ((uint32_t)gi << 8), jb);
+      uint2 th[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int pp = 2 * gi + h; // lanes 2pp, 2pp+1
+        // byte offset = 8 * code, code = (u0 >> 2pp) & 3 | ((u1 >> 2pp) & 3) << 2
+        const int s0 = 2 * pp - 3, s1 = 2 * pp - 5;
+        const uint32_t a0 = s0 >= 0 ? (cnt.u0 >> s0) : (cnt.u0 << (-s0));
+        const uint32_t a1 = s1 >= 0 ? (cnt.u1 >> s1) : (cnt.u1 << (-s1));
+        const uint32_t off = (a0 & 0x18u) | (a1 & 0x60u);
+        th[h] = *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(pair_tab) + pp * 128 + off);
       }
-      F = acc & vmask;
-      own[q] = s0 ^ F;
+      rej = push_reject(rej, r.w, th[1].y);
+      rej = push_reject(rej, r.z, th[1].x);
+      rej = push_reject(rej, r.y, th[0].y);
+      rej = push_reject(rej, r.x, th[0].x);
+    } else {
+      rej <<= 4; // lanes past the last group: not decided here
     }
-    if (ACCUM) {
-      // counts after the flip: flipping s_i toggles every bond of i, so each adder
-      // input, sum and carry plane is toggled by F; the low bit of u is unchanged.
-      uint32_t v1, v2;
-      if (D == 3) {
-        const uint32_t sA2 = sA ^ F, sB2 = sB ^ F, cA2 = cA ^ F, cB2 = cB ^ F;
-        fadd(cA2, cB2, sA2 & sB2, v1, v2);
-      } else {
-        const uint32_t sA2 = sA ^ F, x32 = sB ^ F, cA2 = cA ^ F;
-        const uint32_t tt2 = sA2 & x32;
-        v1 = cA2 ^ tt2;
-        v2 = cA2 & tt2;
-      }
-      vcount_add(V, u0, v1, v2);
+  }
+  return cnt.aut | ~rej;
+}
+
+// Fill the pair tables of one word from its lanes' temperature slots (one warp; lane
+// j's slot in kslot).  Entry (pair p, code) = (thr of lane 2p for u = u0a + 2 u1a,
+// thr of lane 2p+1 for u = u0b + 2 u1b), code = u0a | u0b << 1 | u1a << 2 | u1b << 3.
+// In 2D only the low bit of u selects (u >= 2 is auto-accepted).
+template <int D>
+__device__ __forceinline__ void fill_pair_table(uint2 *pair_tab, int lane, int kslot, int nvalid,
+                                                const uint32_t *thr) {
+  // this lane's four thresholds by u = 0..3 (m = d - u for u < d; 0 otherwise)
+  uint32_t mine[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) mine[u] = (lane < nvalid && u < D) ? thr[kslot * 4 + (D - u)] : 0u;
+  // 256 entries: lane handles pair (lane / 2) ... every (pair, code) via shuffles
+#pragma unroll
+  for (int rep = 0; rep < 8; ++rep) {
+    const int e = rep * 32 + lane;  // entry index 0..255
+    const int pp = e >> 4, code = e & 15;
+    const int ua = D == 3 ? ((code & 1) | ((code >> 1) & 2)) : (code & 1);
+    const int ub = D == 3 ? (((code >> 1) & 1) | ((code >> 2) & 2)) : ((code >> 1) & 1);
+    uint32_t ta = 0, tb = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t va = __shfl_sync(FULL, mine[u], 2 * pp);
+      const uint32_t vb = __shfl_sync(FULL, mine[u], 2 * pp + 1);
+      if (ua == u) ta = va;
+      if (ub == u) tb = vb;
     }
+    pair_tab[pp * 16 + code] = make_uint2(ta, tb);
   }
 }
 
@@ -184,63 +293,214 @@ __device__ __forceinline__ void expand_couplings(const Geo &g, const uint32_t *j
   }
 }
 
-template <int D, int NT, bool FUSE_PT, bool ENERGY_ONLY>
-__global__ void __launch_bounds__(NT) k_resident_packed(Job jb, Dev dv, uint32_t t_metro0,
+// One checkerboard half-sweep over the colour-`col` sites of WPC resident word lattices
+// (all of one sample).  Site geometry, couplings and the site-level Philox parts are
+// shared by the WPC words.  ACCUM adds each site's post-update count to V[w];
+// NOFLIP counts only.
+template <int D, int NT, int WPC, bool ACCUM, bool NOFLIP>
+__device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__restrict__ sp,
+                                           const uint8_t *__restrict__ jbyte,
+                                           const uint2 *__restrict__ pair_tab, const uint32_t *vmask,
+                                           const int *ngroups, const uint32_t *c3base, const PhiloxSweep &P,
+                                           const Job &jb, uint32_t (&V)[WPC][NB]) {
+  const int H = g.H, L1 = g.L1, Nh = g.Nh, N = g.N;
+  for (int q = threadIdx.x; q < Nh; q += NT) {
+    const int row = q / H;
+    const int k = q - row * H;
+    int y, z;
+    if (D == 3) {
+      z = row / L1;
+      y = row - z * L1;
+    } else {
+      y = row;
+      z = 0;
+    }
+    const int xodd = col ^ ((y + z) & 1);
+    const int rb = row * H;
+    int nidx[2 * D];
+    nidx[0] = rb + (xodd ? (k + 1 == H ? 0 : k + 1) : k);
+    nidx[1] = rb + (xodd ? k : (k == 0 ? H - 1 : k - 1));
+    nidx[2] = ((y + 1 == L1) ? row - (L1 - 1) : row + 1) * H + k;
+    nidx[3] = ((y == 0) ? row + (L1 - 1) : row - 1) * H + k;
+    if (D == 3) {
+      const int L2 = g.L2;
+      nidx[4] = ((z + 1 == L2) ? row - (L2 - 1) * L1 : row + L1) * H + k;
+      nidx[5] = ((z == 0) ? row + (L2 - 1) * L1 : row - L1) * H + k;
+    }
+    const uint32_t jsite = jbyte[col * Nh + q];
+    uint32_t jm[2 * D];
+#pragma unroll
+    for (int b = 0; b < 2 * D; ++b) jm[b] = 0u - ((jsite >> b) & 1u);
+    PhiloxSite Q;
+    if (!NOFLIP) Q = philox_site(P, (uint32_t)(g.L0 * row + 2 * k + xodd), jb);
+#pragma unroll
+    for (int w = 0; w < WPC; ++w) {
+      uint32_t *own = sp + w * N + col * Nh;
+      const uint32_t *oth = sp + w * N + (1 - col) * Nh;
+      uint32_t nb[2 * D];
+#pragma unroll
+      for (int b = 0; b < 2 * D; ++b) nb[b] = oth[nidx[b]];
+      const uint32_t s0 = own[q];
+      const SiteCount<D> cnt = count_site<D>(s0, nb, jm);
+      uint32_t F = 0;
+      if (!NOFLIP) {
+        F = decide_site<D>(cnt, P, Q, c3base[w], ngroups[w], pair_tab + w * 256, jb) & vmask[w];
+        own[q] = s0 ^ F;
+      }
+      if (ACCUM) {
+        uint32_t v1, v2;
+        recount<D>(cnt, F, v1, v2);
+        vcount_add(V[w], cnt.u0, v1, v2);
+      }
+    }
+  }
+}
+
+// Replica exchange of one chain from shared memory (Eq. 5), by one warp.  The lanes first
+// draw every pair's word u_k and turn the exact fp64 test into integer bounds on
+// dE = E_k - E_k+1 that are safe by a wide margin (see below); the sequential pass over
+// k = 0..T-2 then compares integers, and only a decision inside the margin (or u = 0)
+// takes the exact path with exp, identical to the standalone kernel and to the oracle.
+//
+// Bounds: with x = u 2^-32 and dbeta = beta_k - beta_k+1 > 0, delta = dbeta dE and the
+// exact rule "accept iff delta >= 0 or x < exp(delta)" is, for dE < 0, "dE > ln(x)/dbeta".
+// With theta = ln(x)/dbeta and margin mg = max(1e-6 (1 + |theta|), 1e-10/(dbeta x)):
+// dE >= theta + mg gives exp(delta) >= x exp(1e-10/x) >= x + 1e-10, and dE <= theta - mg
+// gives x - exp(delta) >= 5e-11, so both fast outcomes agree with the fp64 test and
+// are never within the 1e-12 near-threshold window, whatever the last-bit errors of
+// log, exp and the products.
+__device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, int32_t *pm, int32_t *sl,
+                                                    const int32_t *el, int32_t *accb, int32_t *rejb,
+                                                    uint32_t *uw, unsigned int *pacc, unsigned int *pnear,
+                                                    uint32_t *slowmask, uint32_t s_glob, uint32_t c, uint32_t t,
+                                                    const Job &jb) {
+  const int lane = threadIdx.x & 31;
+  if (lane + 1 < T) {
+    const int k = lane;
+    const uint32_t u = philox10_rk((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, jb.rk0, jb.rk1).x;
+    const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
+    bool slow = (u == 0u);
+    int A = 0, R = 0;
+    if (!slow) {
+      const double x = __dmul_rn((double)u, 0x1p-32);
+      const double theta = log(x) / dbeta;
+      const double mg = fmax(1e-6 * (1.0 + fabs(theta)), 1e-10 / (dbeta * x));
+      const double hi = theta + mg, lo = theta - mg;
+      const double LIM = 1073741824.0; // 2^30, beyond any |dE| <= 2 d N
+      if (!(hi == hi) || !(lo == lo)) {
+        slow = true;
+      } else {
+        A = hi >= LIM ? (int)LIM : (hi <= -LIM ? -(int)LIM : (int)ceil(hi));
+        R = lo <= -LIM ? -(int)LIM : (lo >= LIM ? (int)LIM : (int)floor(lo));
+      }
+    }
+    accb[k] = A;
+    rejb[k] = R;
+    uw[k] = u;
+    const uint32_t sm = __ballot_sync(__activemask(), slow);
+    if (lane == 0) *slowmask = sm;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const uint32_t slowm = T > 1 ? *slowmask : 0u;
+    for (int k = 0; k + 1 < T; ++k) {
+      const int a = pm[k], b = pm[k + 1];
+      const int dE = el[a] - el[b];
+      bool accept;
+      if (dE >= 0) {
+        accept = true;
+      } else if (!((slowm >> k) & 1u) && dE >= accb[k]) {
+        accept = true;
+      } else if (!((slowm >> k) & 1u) && dE <= rejb[k]) {
+        accept = false;
+      } else {
+        const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
+        const double delta = __dmul_rn(dbeta, (double)dE);
+        const double x = __dmul_rn((double)uw[k], 0x1p-32);
+        const double e = exp(delta);
+        if (fabs(__dsub_rn(x, e)) < 1e-12) *pnear += 1u;
+        accept = x < e;
+      }
+      if (accept) {
+        pacc[k] += 1u;
+        pm[k] = b;
+        pm[k + 1] = a;
+        sl[a] = k + 1;
+        sl[b] = k;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <int D, int NT, int WPC, bool FUSE_PT, bool ENERGY_ONLY>
+__global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT) k_resident_packed(Job jb, Dev dv, uint32_t t_metro0,
                                                         uint32_t t_pt0, int n_mcs, int n_metro) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Geo g = jb.g;
-  const PackedSmem L = packed_smem(g.N, g.NW, D, NT);
+  const PackedSmem L = packed_smem(g.N, g.NW, D, NT, WPC);
   uint32_t *sp = reinterpret_cast<uint32_t *>(smem + L.spin);
   uint8_t *jbyte = smem + L.jbyte;
   uint32_t *jpl = reinterpret_cast<uint32_t *>(smem + L.jpl);
-  uint32_t *thr_lane = reinterpret_cast<uint32_t *>(smem + L.thr);
+  uint2 *pair_tab = reinterpret_cast<uint2 *>(smem + L.thr); // [WPC][16 pairs][16 codes]
   int32_t *epart = reinterpret_cast<int32_t *>(smem + L.epart);
-  int32_t *pm = reinterpret_cast<int32_t *>(smem + L.pt);
-  int32_t *sl = pm + 32;
-  int32_t *el = sl + 32;
-  unsigned int *pacc = reinterpret_cast<unsigned int *>(el + 32);
-  unsigned int *pnear = pacc + 32;
+  int32_t *ptw = reinterpret_cast<int32_t *>(smem + L.pt);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+  // per word w: pm, sl, el, pacc, accb, rejb, uw [32 each], then near and slow mask
+  auto PM = [&](int w) { return ptw + w * PT_WORDS; };
+  auto SL = [&](int w) { return ptw + w * PT_WORDS + 32; };
+  auto EL = [&](int w) { return ptw + w * PT_WORDS + 64; };
+  auto PACC = [&](int w) { return reinterpret_cast<unsigned int *>(ptw + w * PT_WORDS + 96); };
+  auto ACCB = [&](int w) { return ptw + w * PT_WORDS + 128; };
+  auto REJB = [&](int w) { return ptw + w * PT_WORDS + 160; };
+  auto UW = [&](int w) { return reinterpret_cast<uint32_t *>(ptw + w * PT_WORDS + 192); };
+  auto NEAR = [&](int w) { return reinterpret_cast<unsigned int *>(ptw + w * PT_WORDS + 224); };
+  auto SLOW = [&](int w) { return reinterpret_cast<uint32_t *>(ptw + w * PT_WORDS + 225); };
 
   const int tid = threadIdx.x;
-  const int item = blockIdx.x;
-  const int s = item / jb.W;
-  const int w = item - s * jb.W;
-  const int c = w / jb.Wc;
-  const int wc = w - c * jb.Wc;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int groups = jb.W / WPC;
+  const int s = blockIdx.x / groups;
+  const int w0 = (blockIdx.x - s * groups) * WPC;
   const uint32_t s_glob = (uint32_t)(jb.s_off + s);
-  const int nvalid = min(32, jb.T - wc * 32);
-  const uint32_t vmask = nvalid >= 32 ? FULL : ((1u << nvalid) - 1u);
-  const int ngroups = (nvalid + 3) >> 2;
-  uint32_t *gsp = dv.spins + ((size_t)s * jb.W + w) * g.N;
+  int ngroups[WPC];
+  uint32_t vmask[WPC], c3base[WPC];
+#pragma unroll
+  for (int w = 0; w < WPC; ++w) {
+    const int cwv = (w0 + w) / jb.Wc;
+    const int wcv = (w0 + w) - cwv * jb.Wc;
+    const int nv = min(32, jb.T - wcv * 32);
+    vmask[w] = nv >= 32 ? FULL : ((1u << nv) - 1u);
+    ngroups[w] = (nv + 3) >> 2;
+    c3base[w] = ((uint32_t)cwv << 20) | ((uint32_t)(wcv * 8) << 8) | TAG_METRO;
+  }
+  uint32_t *gsp = dv.spins + ((size_t)s * jb.W + w0) * g.N; // WPC consecutive word lattices
   const uint32_t *gj = dv.jbits + (size_t)s * D * g.NW;
-  const size_t chain_base = ((size_t)s * jb.C + c) * jb.T;
 
   if (tid == 0) mbar_init(bar, 1);
   __syncthreads();
   if (tid == 0) {
-    const uint32_t sbytes = 4u * (uint32_t)g.N, jbytes = 4u * (uint32_t)(D * g.NW);
+    const uint32_t sbytes = 4u * (uint32_t)(g.N * WPC), jbytes = 4u * (uint32_t)(D * g.NW);
     mbar_expect_tx(bar, sbytes + jbytes);
     bulk_g2s(sp, gsp, sbytes, bar);
     bulk_g2s(jpl, gj, jbytes, bar);
   }
-  if (tid < 32) {
+  // warp w < WPC owns word w0 + w: its chain, replicas and exchange
+  const int my_c = (w0 + warp) / jb.Wc;
+  const int my_wc = (w0 + warp) - my_c * jb.Wc;
+  const int my_nvalid = min(32, jb.T - my_wc * 32);
+  const size_t my_cb = ((size_t)s * jb.C + my_c) * jb.T;
+  if (warp < WPC) {
+    const int w = warp;
     if (FUSE_PT) {
-      pm[tid] = tid < jb.T ? dv.perm[chain_base + tid] : 0;
-      sl[tid] = tid < jb.T ? dv.slot[chain_base + tid] : 0;
-      pacc[tid] = 0u;
-      if (tid == 0) *pnear = 0u;
+      PM(w)[lane] = lane < jb.T ? dv.perm[my_cb + lane] : 0;
+      SL(w)[lane] = lane < jb.T ? dv.slot[my_cb + lane] : 0;
+      PACC(w)[lane] = 0u;
+      if (lane == 0) *NEAR(w) = 0u;
     }
     if (!ENERGY_ONLY) {
-      const int j = wc * 32 + tid;
-      uint32_t tv[4] = {0u, 0u, 0u, 0u};
-      if (tid < nvalid) {
-        const int kslot = FUSE_PT ? sl[tid] : dv.slot[chain_base + j];
-#pragma unroll
-        for (int idx = 0; idx < D; ++idx) tv[idx] = dv.thr[kslot * 4 + (D - idx)];
-      }
-#pragma unroll
-      for (int idx = 0; idx < 4; ++idx) thr_lane[tid * 4 + idx] = tv[idx];
+      const int kslot = lane < my_nvalid ? (FUSE_PT ? SL(w)[lane] : dv.slot[my_cb + my_wc * 32 + lane]) : 0;
+      fill_pair_table<D>(pair_tab + w * 256, lane, kslot, my_nvalid, dv.thr);
     }
   }
   const bool ok = mbar_wait(bar, 0, MBAR_MAX_TRIES);
@@ -254,59 +514,61 @@ __global__ void __launch_bounds__(NT) k_resident_packed(Job jb, Dev dv, uint32_t
   expand_couplings<D, NT>(g, jpl, jbyte);
   __syncthreads();
 
-  const uint32_t c3base = ((uint32_t)c << 20) | ((uint32_t)(wc * 8) << 8) | TAG_METRO;
   const int n_outer = ENERGY_ONLY ? 1 : n_mcs;
   const int n_inner = ENERGY_ONLY ? 1 : n_metro;
   for (int m = 0; m < n_outer; ++m) {
     for (int swp = 0; swp < n_inner; ++swp) {
       const uint32_t t = t_metro0 + (uint32_t)(m * n_metro + swp);
-      uint32_t V[NB];
+      const PhiloxSweep P = philox_sweep(s_glob, t, jb);
+      uint32_t V[WPC][NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) V[b] = 0u;
+      for (int w = 0; w < WPC; ++w)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) V[w][b] = 0u;
       if (!ENERGY_ONLY) {
-        half_sweep<D, NT, false, false>(g, 0, sp, jbyte, thr_lane, vmask, ngroups, t, s_glob, c3base,
-                                        jb.sk0, jb.sk1, V);
+        half_sweep<D, NT, WPC, false, false>(g, 0, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
         __syncthreads();
       }
-      half_sweep<D, NT, true, ENERGY_ONLY>(g, 1, sp, jbyte, thr_lane, vmask, ngroups, t, s_glob, c3base,
-                                           jb.sk0, jb.sk1, V);
-      const int32_t part = warp_lane_sum(V);
-      epart[tid] = part; // warp (tid / 32), lane (tid % 32)
+      half_sweep<D, NT, WPC, true, ENERGY_ONLY>(g, 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
+#pragma unroll
+      for (int w = 0; w < WPC; ++w) epart[w * NT + tid] = warp_lane_sum(V[w]);
       __syncthreads();
-      if (tid < 32) {
+      if (warp < WPC) {
         int32_t U = 0;
-        for (int wq = 0; wq < NT / 32; ++wq) U += epart[wq * 32 + tid];
-        el[tid] = 2 * U - D * g.N;
+        for (int wq = 0; wq < NT / 32; ++wq) U += epart[warp * NT + wq * 32 + lane];
+        EL(warp)[lane] = 2 * U - D * g.N;
       }
-      __syncthreads();
+      if (!FUSE_PT || swp + 1 < n_inner) __syncthreads();
     }
     if (FUSE_PT) {
-      if (tid == 0)
-        exchange_chain(jb.T, dv.beta, pm, sl, el, s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb.sk0, jb.sk1,
-                       [&](int k) { pacc[k] += 1u; }, [&]() { *pnear += 1u; });
-      __syncthreads();
-      if (tid < nvalid) {
-        const int kslot = sl[tid];
-#pragma unroll
-        for (int idx = 0; idx < D; ++idx) thr_lane[tid * 4 + idx] = dv.thr[kslot * 4 + (D - idx)];
+      // warp w exchanges chain w (one chain per word), then refreshes its lanes' thresholds
+      if (warp < WPC) {
+        const int w = warp;
+        __syncwarp();
+        exchange_chain_smem(jb.T, dv.beta, PM(w), SL(w), EL(w), ACCB(w), REJB(w), UW(w), PACC(w), NEAR(w),
+                            SLOW(w), s_glob, (uint32_t)my_c, t_pt0 + (uint32_t)m, jb);
+        if (!ENERGY_ONLY) fill_pair_table<D>(pair_tab + w * 256, lane, lane < my_nvalid ? SL(w)[lane] : 0, my_nvalid, dv.thr);
       }
       __syncthreads();
     }
   }
 
-  if (tid < nvalid) dv.E[chain_base + wc * 32 + tid] = el[tid];
-  if (FUSE_PT && tid < 32) {
-    if (tid < jb.T) {
-      dv.perm[chain_base + tid] = pm[tid];
-      dv.slot[chain_base + tid] = sl[tid];
+  if (warp < WPC) {
+    const int w = warp;
+    if (lane < my_nvalid) dv.E[my_cb + my_wc * 32 + lane] = EL(w)[lane];
+    if (FUSE_PT) {
+      if (lane < jb.T) {
+        dv.perm[my_cb + lane] = PM(w)[lane];
+        dv.slot[my_cb + lane] = SL(w)[lane];
+      }
+      if (lane + 1 < jb.T && PACC(w)[lane]) atomicAdd(&dv.ctr[CTR_PT + lane], (unsigned long long)PACC(w)[lane]);
+      if (lane == 0 && *NEAR(w)) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*NEAR(w));
     }
-    if (tid + 1 < jb.T && pacc[tid]) atomicAdd(&dv.ctr[CTR_PT + tid], (unsigned long long)pacc[tid]);
-    if (tid == 0 && *pnear) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*pnear);
   }
   if (!ENERGY_ONLY) {
     fence_proxy_async(); // this thread's shared-memory writes -> visible to the TMA store
     __syncthreads();
-    if (tid == 0) bulk_s2g_and_wait(gsp, sp, 4u * (uint32_t)g.N);
+    if (tid == 0) bulk_s2g_and_wait(gsp, sp, 4u * (uint32_t)(g.N * WPC));
   }
 }
 
@@ -494,16 +756,20 @@ __global__ void k_exchange(Job jb, Dev dv, uint32_t t_pt) {
 namespace {
 typedef void (*resident_fn)(Job, Dev, uint32_t, uint32_t, int, int);
 
-template <bool FUSE, bool EONLY>
-resident_fn pick_packed(int d, int nt) {
-  if (d == 2) {
-    if (nt == 256) return k_resident_packed<2, 256, FUSE, EONLY>;
-    if (nt == 512) return k_resident_packed<2, 512, FUSE, EONLY>;
-    return k_resident_packed<2, 1024, FUSE, EONLY>;
+template <int D, int WPC, bool FUSE, bool EONLY>
+resident_fn pick_packed_nt(int nt) {
+  switch (nt) {
+  case 128: return k_resident_packed<D, 128, WPC, FUSE, EONLY>;
+  case 256: return k_resident_packed<D, 256, WPC, FUSE, EONLY>;
+  case 512: return k_resident_packed<D, 512, WPC, FUSE, EONLY>;
+  default: return k_resident_packed<D, 1024, WPC, FUSE, EONLY>;
   }
-  if (nt == 256) return k_resident_packed<3, 256, FUSE, EONLY>;
-  if (nt == 512) return k_resident_packed<3, 512, FUSE, EONLY>;
-  return k_resident_packed<3, 1024, FUSE, EONLY>;
+}
+
+template <bool FUSE, bool EONLY>
+resident_fn pick_packed(int d, int nt, int wpc) {
+  if (d == 2) return wpc == 2 ? pick_packed_nt<2, 2, FUSE, EONLY>(nt) : pick_packed_nt<2, 1, FUSE, EONLY>(nt);
+  return wpc == 2 ? pick_packed_nt<3, 2, FUSE, EONLY>(nt) : pick_packed_nt<3, 1, FUSE, EONLY>(nt);
 }
 
 template <bool FUSE, bool EONLY>
@@ -512,22 +778,26 @@ resident_fn pick_int8(int d) {
 }
 
 template <bool FUSE, bool EONLY>
-resident_fn pick(bool int8fmt, int d, int nt) {
-  return int8fmt ? pick_int8<FUSE, EONLY>(d) : pick_packed<FUSE, EONLY>(d, nt);
+resident_fn pick(bool int8fmt, int d, int nt, int wpc) {
+  return int8fmt ? pick_int8<FUSE, EONLY>(d) : pick_packed<FUSE, EONLY>(d, nt, wpc);
 }
 } // namespace
 
-cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, bool fuse_pt,
+cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0,
                             int n_mcs, int n_metro) {
   resident_fn fn;
-  if (energy_only) fn = pick<false, true>(int8fmt, jb.g.d, nthreads);
-  else if (fuse_pt) fn = pick<true, false>(int8fmt, jb.g.d, nthreads);
-  else fn = pick<false, false>(int8fmt, jb.g.d, nthreads);
-  if (int8fmt) nthreads = 256;
+  if (energy_only && fuse_pt) fn = pick<true, true>(int8fmt, jb.g.d, nthreads, wpc);
+  else if (energy_only) fn = pick<false, true>(int8fmt, jb.g.d, nthreads, wpc);
+  else if (fuse_pt) fn = pick<true, false>(int8fmt, jb.g.d, nthreads, wpc);
+  else fn = pick<false, false>(int8fmt, jb.g.d, nthreads, wpc);
+  if (int8fmt) {
+    nthreads = 256;
+    wpc = 1;
+  }
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = int8fmt ? (unsigned)(jb.S * jb.C) : (unsigned)(jb.S * jb.W);
+  const unsigned grid = int8fmt ? (unsigned)(jb.S * jb.C) : (unsigned)(jb.S * (jb.W / wpc));
   fn<<<grid, nthreads, smem, st>>>(jb, dv, t_metro0, t_pt0, n_mcs, n_metro);
   return cudaGetLastError();
 }

@@ -37,6 +37,7 @@ struct sg_handle {
   sg_status sticky;
   int int8fmt;
   int nt;          // threads of the resident kernel
+  int wpc;         // 32-replica words per CTA of the packed resident kernel
   size_t smem;     // its dynamic shared memory
   bool fuse_pt;    // the exchange can run inside the resident kernel
   int n_ctr;       // counters in the device array
@@ -92,6 +93,10 @@ void build_job(const sg_params *p, Job *jb) {
   jb->sk1 = (uint32_t)(p->sim_seed >> 32);
   jb->ck0 = (uint32_t)(p->coupling_seed & 0xFFFFFFFFu);
   jb->ck1 = (uint32_t)(p->coupling_seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    jb->rk0[r] = jb->sk0 + (uint32_t)r * PH_W0;
+    jb->rk1[r] = jb->sk1 + (uint32_t)r * PH_W1;
+  }
   double cut = std::floor(std::ldexp(p->p_plus, 32));
   if (cut < 0.0) cut = 0.0;
   if (cut > 4294967296.0) cut = 4294967296.0;
@@ -135,24 +140,45 @@ int max_dyn_smem() {
   return v;
 }
 
-// Choose the resident kernel's CTA size: the smallest of 256/512/1024 threads whose
-// per-thread colour-1 sites keep the 8-plane vertical counter below 256.
+// Whether the packed resident kernel can run with this shape: the per-thread colour-1
+// sites must keep the 8-plane vertical counter below 256, the words per CTA must divide
+// the sample's words, and the lattice must fit in shared memory.
+bool packed_shape_ok(const sg_handle *h, int nt, int wpc, int smem_limit, size_t *smem) {
+  const Geo &g = h->job.g;
+  if (nt != 128 && nt != 256 && nt != 512 && nt != 1024) return false;
+  if (wpc != 1 && wpc != 2) return false;
+  if (h->job.W % wpc) return false;
+  const int per_thread = (g.Nh + nt - 1) / nt;
+  if (per_thread * 2 * g.d > 255) return false;
+  const PackedSmem L = packed_smem(g.N, g.NW, g.d, nt, wpc);
+  if (L.total > smem_limit) return false;
+  *smem = (size_t)L.total;
+  return true;
+}
+
+// Choose the resident kernel's default shape: two words per CTA (one sample's two
+// chains) when two such CTAs fit on an SM, else one; the smallest CTA of 256/512/1024
+// threads whose counters do not overflow.
 bool choose_resident(sg_handle *h, int smem_limit) {
   const Geo &g = h->job.g;
   if (h->int8fmt) {
     const Int8Smem L = int8_smem(g.N, g.NW, g.d, h->job.T, h->job.Tp);
     h->nt = 256;
+    h->wpc = 1;
     h->smem = (size_t)L.total;
     return L.total <= smem_limit;
   }
-  for (int nt : {256, 512, 1024}) {
-    const int per_thread = (g.Nh + nt - 1) / nt;
-    if (per_thread * 2 * g.d > 255) continue;
-    const PackedSmem L = packed_smem(g.N, g.NW, g.d, nt);
-    if (L.total > smem_limit) return false;
-    h->nt = nt;
-    h->smem = (size_t)L.total;
-    return true;
+  // two words per CTA (one sample's two chains) when they fit: the site geometry, the
+  // couplings and the site-level Philox work are then shared by 64 replicas
+  for (int wpc : {2, 1}) {
+    for (int nt : {256, 512, 1024}) {
+      size_t sm = 0;
+      if (!packed_shape_ok(h, nt, wpc, wpc == 2 ? smem_limit / 2 : smem_limit, &sm)) continue;
+      h->nt = nt;
+      h->wpc = wpc;
+      h->smem = sm;
+      return true;
+    }
   }
   return false;
 }
@@ -168,7 +194,7 @@ sg_status check(sg_handle *h, cudaError_t e) {
 template <bool FUSE, bool EONLY>
 sg_status launch_resident(sg_handle *h, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0, int n_mcs,
                           int n_metro) {
-  return check(h, sgmc::launch_resident(h->job, h->dev, h->int8fmt != 0, h->nt, FUSE, EONLY, h->smem, st,
+  return check(h, sgmc::launch_resident(h->job, h->dev, h->int8fmt != 0, h->nt, h->wpc, FUSE, EONLY, h->smem, st,
                                         t_metro0, t_pt0, n_mcs, n_metro));
 }
 
@@ -423,6 +449,27 @@ sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out) {
   const int d = h->job.g.d;
   for (int k = 0; k < h->job.T; ++k)
     for (int m = 1; m <= d; ++m) thr_out[k * d + (m - 1)] = h->thr[(size_t)k * 4 + m];
+  return SG_OK;
+}
+
+sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words) {
+  if (!h) return SG_EINVAL;
+  if (h->int8fmt) return (threads == 0 || threads == 256) && (words == 0 || words == 1) ? SG_OK : SG_EUNSUPPORTED;
+  const int nt = threads ? threads : h->nt;
+  const int wpc = words ? words : h->wpc;
+  size_t sm = 0;
+  if (!packed_shape_ok(h, nt, wpc, max_dyn_smem(), &sm)) return SG_EUNSUPPORTED;
+  h->nt = nt;
+  h->wpc = wpc;
+  h->smem = sm;
+  return SG_OK;
+}
+
+sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t *smem_bytes) {
+  if (!h) return SG_EINVAL;
+  if (threads) *threads = h->nt;
+  if (words) *words = h->wpc;
+  if (smem_bytes) *smem_bytes = (int32_t)h->smem;
   return SG_OK;
 }
 

@@ -50,6 +50,7 @@ struct Job {
   uint32_t sk0, sk1;       // sim_seed as a Philox key
   uint32_t ck0, ck1;       // coupling_seed as a Philox key
   unsigned long long jcut; // J = +1 iff the word is below this (floor(p 2^32), up to 2^32)
+  uint32_t rk0[10], rk1[10]; // sim_seed round keys (k + r W) so kernels read them as constants
 };
 
 struct Dev {
@@ -85,6 +86,23 @@ __device__ __forceinline__ uint4 philox10(uint32_t x0, uint32_t x1, uint32_t x2,
     x3 = lo0;
     k0 += PH_W0;
     k1 += PH_W1;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+// Philox4x32-10 with the ten round keys given explicitly (kernel-parameter arrays).
+__device__ __forceinline__ uint4 philox10_rk(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                             const uint32_t *rk0, const uint32_t *rk1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(PH_M0, x0), lo0 = PH_M0 * x0;
+    const uint32_t hi1 = __umulhi(PH_M1, x2), lo1 = PH_M1 * x2;
+    const uint32_t y0 = hi1 ^ x1 ^ rk0[r];
+    const uint32_t y2 = hi0 ^ x3 ^ rk1[r];
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
   }
   return make_uint4(x0, x1, x2, x3);
 }
@@ -194,19 +212,22 @@ namespace sgmc {
 
 __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 
-// Shared-memory map of the resident packed kernel (one 32-replica word lattice).
+// Shared-memory map of the resident packed kernel: `wpc` 32-replica word lattices of one
+// sample, its expanded couplings, per-lane threshold tables, energy partial sums and the
+// per-chain exchange scratch.
+constexpr int PT_WORDS = 7 * 32 + 4; // per word: perm, slot, E, accepts, accept/reject bounds, u; flags
 struct PackedSmem {
   int spin, jbyte, jpl, thr, epart, pt, bar, total;
 };
-__host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthreads) {
+__host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthreads, int wpc) {
   PackedSmem L;
   L.spin = 0;
-  L.jbyte = L.spin + 4 * N;
+  L.jbyte = L.spin + 4 * N * wpc;
   L.jpl = L.jbyte + round16(N);
   L.thr = L.jpl + round16(4 * d * NW);
-  L.epart = L.thr + 32 * 4 * 4;
-  L.pt = L.epart + 4 * nthreads;
-  L.bar = L.pt + round16(4 * 32 * 4 + 16);
+  L.epart = L.thr + wpc * 256 * 8; // lane-pair threshold tables, 16 pairs x 16 codes x 8 bytes
+  L.pt = L.epart + 4 * nthreads * wpc;
+  L.bar = L.pt + round16(4 * PT_WORDS * wpc);
   L.total = L.bar + 16;
   return L;
 }
@@ -232,7 +253,7 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 }
 
 // Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
-cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, bool fuse_pt,
+cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0,
                             int n_mcs, int n_metro);
 cudaError_t launch_exchange(const Job &jb, const Dev &dv, uint32_t t_pt, cudaStream_t st);

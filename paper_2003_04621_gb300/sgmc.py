@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_run_mcs", "sg_measure",
     "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
-    "sg_get_state", "sg_counters", "sg_thresholds", "sg_destroy", "sg_strerror",
+    "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_destroy", "sg_strerror",
 )
 
 _lib = None
@@ -83,6 +83,8 @@ def lib():
         "sg_get_state": [P, P, P, P, U],
         "sg_counters": [P, P, P, P, U],
         "sg_thresholds": [P, P],
+        "sg_set_launch": [P, I32, I32],
+        "sg_get_launch": [P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -258,6 +260,17 @@ class Simulation:
                "sg_counters")
         return {"near_threshold": int(near[0]), "pt_accepts": acc[: self.T - 1].copy(),
                 "houdayer_sites": int(hs[0])}
+
+    def set_launch(self, threads: int = 0, words: int = 0):
+        """Resident-kernel launch shape (threads per CTA, words per CTA); results are
+        identical for every accepted shape."""
+        _check(lib().sg_set_launch(self._h, int(threads), int(words)), "sg_set_launch")
+
+    def launch(self):
+        v = np.zeros(3, np.int32)
+        _check(lib().sg_get_launch(self._h, v[0:].ctypes.data, v[1:].ctypes.data, v[2:].ctypes.data),
+               "sg_get_launch")
+        return {"threads": int(v[0]), "words": int(v[1]), "smem": int(v[2])}
 
     def thresholds(self) -> np.ndarray:
         out = np.zeros((self.T, self.ndim), np.uint32)

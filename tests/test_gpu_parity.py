@@ -260,3 +260,25 @@ def test_status_codes_on_device():
     assert st in (0, 5)
     if st == 0:
         L.sg_destroy(hb)
+
+
+@pytest.mark.parametrize("ndim,dims,T", [(3, (16, 16, 16), 32), (2, (32, 48), 24), (3, (6, 8, 4), 40)])
+def test_every_launch_shape_gives_identical_results(oracle_mod, ndim, dims, T):
+    """The resident kernel's CTA size and words per CTA are tuning knobs only."""
+    kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.5, 2.0, T), sim_seed=3)
+    orc = oracle_of(oracle_mod, **_oracle_kw(kw))
+    orc.mcs(3)
+    ran = 0
+    from paper_2003_04621_gb300.sgmc import SGError
+
+    for nt in (128, 256, 512, 1024):
+        for words in (1, 2):
+            sim = gpu_of(**kw)
+            try:
+                sim.set_launch(nt, words)
+            except SGError:
+                continue
+            sim.run_mcs(3)
+            assert_same_state(sim, orc, f"threads={nt} words={words}")
+            ran += 1
+    assert ran >= 2
