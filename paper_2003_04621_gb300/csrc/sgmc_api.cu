@@ -14,7 +14,7 @@ using namespace sgmc;
 namespace {
 
 struct Layout {
-  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, total;
+  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, houd, houd_bytes, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -103,6 +103,12 @@ void build_job(const sg_params *p, Job *jb) {
   jb->jcut = (unsigned long long)cut;
 }
 
+// The Houdayer kernel pairs lanes of one chain-0 and one chain-1 word: packed spins, two
+// chains, at most 32 temperatures, rows of at most 256 sites.
+bool houdayer_possible(const sg_params *p, const Job &jb) {
+  return p->spin_format == SG_PACKED32 && jb.C == 2 && jb.Wc == 1 && jb.g.L0 <= 256 && jb.g.R <= 65535;
+}
+
 Layout layout_of(const sg_params *p, const Job &jb) {
   const Geo &g = jb.g;
   const size_t S = (size_t)jb.S, C = (size_t)jb.C, T = (size_t)jb.T, N = (size_t)g.N;
@@ -124,6 +130,10 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   L.ctr = take((size_t)(CTR_PT + T) * 8);
   L.meas_E = take(S * C * T * 4);
   L.meas_Q = take(S * T * 4);
+  // Houdayer bitmaps that do not fit the kernel's shared-memory budget
+  L.houd_bytes = 0;
+  if (houdayer_possible(p, jb) && houdayer_smem(jb, 1) > HOUD_SMEM_BUDGET) L.houd_bytes = houdayer_scratch_bytes(jb);
+  L.houd = take(L.houd_bytes);
   L.total = off;
   return L;
 }
@@ -215,6 +225,15 @@ sg_status exchange(sg_handle *h, cudaStream_t st) {
 
 sg_status recompute_energy(sg_handle *h, cudaStream_t st) {
   return launch_resident<false, true>(h, st, 0u, 0u, 1, 1);
+}
+
+// The cluster move itself (spins only; energies are stale until recomputed).
+sg_status houdayer_move(sg_handle *h, cudaStream_t st) {
+  uint32_t *scratch = h->lay.houd_bytes ? reinterpret_cast<uint32_t *>(h->buf + h->lay.houd) : nullptr;
+  const int limit = h->lay.houd_bytes ? 0 : HOUD_SMEM_BUDGET;
+  sg_status r = check(h, launch_houdayer(h->job, h->dev, (uint32_t)h->t_houd, scratch, limit, st));
+  if (r == SG_OK) h->t_houd += 1;
+  return r;
 }
 
 // Read the device error word; poison the handle if a bounded wait expired.
@@ -328,9 +347,11 @@ sg_status sg_exchange(sg_handle *h, uintptr_t stream) {
 sg_status sg_houdayer(sg_handle *h, uintptr_t stream) {
   if (!h) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
-  (void)stream;
   if (h->job.C != 2) return SG_EINVAL;
-  return SG_EUNSUPPORTED;
+  if (!houdayer_possible(&h->p, h->job)) return SG_EUNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  sg_status r = houdayer_move(h, st);
+  return r == SG_OK ? recompute_energy(h, st) : r;
 }
 
 sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
@@ -347,9 +368,20 @@ sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
     }
     return r;
   }
+  if (h->p.houdayer && !houdayer_possible(&h->p, h->job)) return SG_EUNSUPPORTED;
   for (int m = 0; m < n_mcs; ++m) {
     sg_status r = sweeps(h, nm, st);
-    if (r == SG_OK && h->p.houdayer) r = sg_houdayer(h, stream);
+    if (r == SG_OK && h->p.houdayer) {
+      r = houdayer_move(h, st);
+      if (r == SG_OK && h->fuse_pt) {
+        // energies after the move, then the exchange, in one resident launch
+        r = launch_resident<true, true>(h, st, 0u, (uint32_t)h->t_pt, 1, 1);
+        if (r == SG_OK) h->t_pt += 1;
+        if (r != SG_OK) return r;
+        continue;
+      }
+      if (r == SG_OK) r = recompute_energy(h, st);
+    }
     if (r == SG_OK) r = exchange(h, st);
     if (r != SG_OK) return r;
   }

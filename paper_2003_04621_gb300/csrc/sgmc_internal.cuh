@@ -33,6 +33,12 @@ constexpr int CTR_HMOVES = 3; // Houdayer moves with M > 0
 constexpr int CTR_PT = 4;     // [T-1] accepted exchanges per pair
 
 constexpr unsigned long long ERR_TMA_TIMEOUT = 1ull;
+constexpr unsigned long long ERR_HOUD_ROUNDS = 2ull; // a cluster fill hit its round limit (never expected)
+
+// Shared-memory budget the Houdayer kernel's bitmaps may use; above it they go to a
+// scratch region of the caller's buffer.  A fixed number (not the device's) so that the
+// buffer size does not depend on the device.
+constexpr int HOUD_SMEM_BUDGET = 200 * 1024;
 
 struct Geo {
   int d;          // 2 or 3
@@ -257,6 +263,10 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
                             bool energy_only, size_t smem, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0,
                             int n_mcs, int n_metro);
 cudaError_t launch_exchange(const Job &jb, const Dev &dv, uint32_t t_pt, cudaStream_t st);
+int houdayer_smem(const Job &jb, int bitmaps_smem);
+size_t houdayer_scratch_bytes(const Job &jb);
+cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t t_houd, uint32_t *scratch, int smem_limit,
+                            cudaStream_t st);
 } // namespace sgmc
 
 namespace sgmc {

@@ -1,0 +1,120 @@
+"""GPU parity of the Houdayer cluster move (Sec. 2.4, Eq. 10) against the oracle.
+
+Every (sample, temperature slot) pair chooses its seed from its own Philox word and the
+floor(u M / 2^32)-th q = -1 site in site order; the cluster is the seed's connected q = -1
+component, grown on the GPU row by row (periodic runs, queue of rows) and by breadth-
+first search in the oracle.  After every step the spins, energies, replica maps, N q and
+the number of flipped sites must be identical.
+"""
+import numpy as np
+import pytest
+
+from helpers import assert_same_state, gpu_of, oracle_of
+from paper_2003_04621_gb300.inputs import geometric_temps, workload_2d_l128_houdayer
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2003_04621_gb300 import build
+
+    build.build()
+
+
+def _okw(kw):
+    return {k: v for k, v in kw.items() if k not in ("spin_format", "houdayer", "n_metro")}
+
+
+def run_pair(oracle_mod, kw, ops, check_every=1):
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    for t, op in enumerate(ops):
+        if op == "s":
+            sim.sweep(1)
+            orc.sweep(1)
+        elif op == "h":
+            sim.houdayer()
+            orc.houdayer()
+        elif op == "x":
+            sim.exchange()
+            orc.exchange()
+        elif op == "m":
+            sim.run_mcs(1)
+            orc.mcs(1, houdayer=bool(kw.get("houdayer", False)))
+        if t % check_every == 0 or t == len(ops) - 1:
+            assert_same_state(sim, orc, f"step {t} ({op})")
+    c = orc.counters()
+    assert c["error"] == 0
+    assert sim.counters()["houdayer_sites"] == c["houd_flipped"]
+    return sim, orc
+
+
+@pytest.mark.parametrize("dims", [(16, 16), (40, 24), (66, 4), (2, 8), (8, 2), (96, 6)])
+def test_houdayer_calls_2d(oracle_mod, dims):
+    kw = dict(ndim=2, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.2, 1.6, 8), sim_seed=7,
+              coupling_seed=5)
+    run_pair(oracle_mod, kw, list("sshxshhxsxh"))
+
+
+@pytest.mark.parametrize("dims,T", [((8, 8, 8), 12), ((4, 6, 2), 32), ((16, 4, 8), 5)])
+def test_houdayer_calls_3d(oracle_mod, dims, T):
+    kw = dict(ndim=3, dims=dims, n_samples=2, n_chains=2, temps=geometric_temps(0.5, 2.5, T), sim_seed=19)
+    run_pair(oracle_mod, kw, list("shxshhx"))
+
+
+def test_houdayer_mcs_2d_l128(oracle_mod):
+    """2D L=128 x 24 temperatures in [0.2, 1.6], Metropolis + Houdayer + exchange per
+    MCS: two samples of the 256-sample job, compared after every MCS."""
+    w = workload_2d_l128_houdayer()
+    kw = dict(ndim=2, dims=w.dims, n_samples=2, n_chains=2, temps=list(w.temps), sim_seed=w.sim_seed,
+              coupling_seed=w.coupling_seed, sample_offset=200, houdayer=True)
+    sim, orc = run_pair(oracle_mod, kw, ["m"] * 6)
+    assert orc.counters()["houd_moves"] > 0
+
+
+def test_houdayer_cold_percolating_clusters(oracle_mod):
+    """Low temperatures and a q field of many large clusters (chains started apart)."""
+    kw = dict(ndim=2, dims=(64, 32), n_samples=2, n_chains=2, temps=geometric_temps(0.05, 0.3, 6), sim_seed=3,
+              houdayer=True)
+    run_pair(oracle_mod, kw, ["m"] * 8)
+
+
+def test_houdayer_bitmaps_in_global_scratch(oracle_mod):
+    """3D L=32 x 32 temperatures: the pair bitmaps exceed the shared-memory budget and live
+    in the scratch region of the handle's buffer."""
+    kw = dict(ndim=3, dims=(32, 32, 32), n_samples=1, n_chains=2, temps=geometric_temps(0.9, 2.0, 32),
+              sim_seed=2, houdayer=True)
+    run_pair(oracle_mod, kw, ["m", "m"])
+
+
+def test_houdayer_full_size_sampled(oracle_mod):
+    """The whole 256-sample 2D L=128 job on the GPU; two samples recomputed by the oracle."""
+    w = workload_2d_l128_houdayer()
+    kw = dict(ndim=2, dims=w.dims, n_samples=w.n_samples, n_chains=2, temps=list(w.temps), sim_seed=w.sim_seed,
+              coupling_seed=w.coupling_seed, houdayer=True)
+    sim = gpu_of(**kw)
+    picks = [3, 255]
+    orcs = [oracle_of(oracle_mod, **_okw(dict(kw, n_samples=1, sample_offset=s))) for s in picks]
+    for t in range(3):
+        sim.run_mcs(1)
+        E, perm, _ = sim.state()
+        Em, Q = sim.measure()
+        for s, o in zip(picks, orcs):
+            o.mcs(1, houdayer=True)
+            np.testing.assert_array_equal(E[s:s + 1], o.energies())
+            np.testing.assert_array_equal(perm[s:s + 1], o.perm()[0])
+            np.testing.assert_array_equal(Q[s:s + 1], o.measure()[1])
+    assert sim.counters()["near_threshold"] == 0
+
+
+def test_houdayer_refused_where_unsupported():
+    from paper_2003_04621_gb300.sgmc import SGError
+
+    sim = gpu_of(ndim=2, dims=(8, 8), n_samples=1, n_chains=2, temps=geometric_temps(0.5, 2.0, 40))
+    with pytest.raises(SGError) as e:
+        sim.houdayer()
+    assert e.value.status == 5
+    one = gpu_of(ndim=2, dims=(8, 8), n_samples=1, n_chains=1, temps=[1.0, 2.0])
+    with pytest.raises(SGError) as e:
+        one.houdayer()
+    assert e.value.status == 1
