@@ -158,14 +158,30 @@ sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out);
 
 /* Launch shape of the resident sweep kernel (not part of the paper: a tuning knob).
  *   threads  CTA size: 128, 256, 512 or 1024 (0 keeps the current choice)
- *   words    32-replica words of one sample held by one CTA: 1 or 2 (0 keeps)
+ *   words    32-replica words of one sample held by one CTA: 1 or 2 (0 keeps);
+ *            -1 streams the lattice from global memory instead of keeping it in a CTA
+ *            (the path taken automatically when a word lattice does not fit)
  * Every accepted choice gives bit-identical results; a shape that does not fit the
  * lattice (shared memory, per-thread counter range, word count) is refused with
  * SG_EUNSUPPORTED and the previous shape is kept.  Host-only; no device work. */
 sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words);
 
-/* Current launch shape: threads, words per CTA, dynamic shared memory bytes. */
+/* Current launch shape: threads, words per CTA (-1: streaming path), shared memory bytes. */
 sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t *smem_bytes);
+
+/* Batches (not a step of the paper's method: a way to run many jobs at once).  The MCS
+ * cycles of n_handles jobs (any mix of lattices, temperatures and sample counts) are
+ * captured once into one CUDA graph, mcs_per_launch MCS per job per launch, each job a
+ * branch of the graph so that the jobs' kernels run concurrently.  Each job advances
+ * exactly as it would under sg_run_mcs (bit-identical results).  The handles must
+ * outlive the batch and must not be used by other calls while its launches run;
+ * sg_batch_create enqueues nothing, sg_batch_run enqueues n_launches graph launches
+ * on `stream`. */
+typedef struct sg_batch sg_batch;
+sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t mcs_per_launch,
+                          uintptr_t stream, sg_batch **out);
+sg_status sg_batch_run(sg_batch *b, int32_t n_launches, uintptr_t stream);
+void sg_batch_destroy(sg_batch *b);
 
 /* Free the host-side handle.  The caller frees the device buffer afterwards. */
 void sg_destroy(sg_handle *h);

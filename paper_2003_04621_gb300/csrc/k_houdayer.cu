@@ -138,7 +138,6 @@ __device__ __forceinline__ void close_row(const uint32_t (&Q)[RW], const uint32_
 } // namespace
 
 struct HoudArgs {
-  uint32_t t_houd;
   int RW;           // words per bitmap row
   int NBW;          // words per bitmap (rows x RW)
   int bitmaps_smem; // 1: q and cluster bitmaps in shared memory, 0: in `scratch`
@@ -175,6 +174,7 @@ __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
   unsigned long long *cnts = reinterpret_cast<unsigned long long *>(Mc + 32); // moves, sites
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t t_houd = (uint32_t)dv.ctr[CTR_THOUD];
   const int s = blockIdx.x;
   const uint32_t s_glob = (uint32_t)(jb.s_off + s);
   uint32_t *Qb, *Cb;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
     const uint32_t M = Mc[a];
     if (M == 0u) continue;
     const int k = slot0[a];
-    const uint32_t u = philox10((uint32_t)k, ha.t_houd, s_glob, TAG_HOUD, jb.sk0, jb.sk1).x;
+    const uint32_t u = philox10((uint32_t)k, t_houd, s_glob, TAG_HOUD, jb.sk0, jb.sk1).x;
     const uint32_t n = (uint32_t)(((unsigned long long)u * M) >> 32);
     // the n-th set bit in canonical order: contiguous chunks per lane, then a warp scan
     const int chunk = (NBW + 31) / 32;
@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
     if (cnts[0]) atomicAdd(&dv.ctr[CTR_HMOVES], cnts[0]);
     if (cnts[1]) atomicAdd(&dv.ctr[CTR_HSITES], cnts[1]);
   }
+  grid_done_advance(dv.ctr, 0ull, 0ull, 1ull);
 }
 
 int houdayer_smem(const Job &jb, int bitmaps_smem) {
@@ -425,10 +426,20 @@ houd_fn pick_houd(int RW) {
 }
 } // namespace
 
-cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t t_houd, uint32_t *scratch, int smem_limit,
-                            cudaStream_t st) {
+cudaError_t prepare_houdayer_kernels(int max_smem) {
+  for (int rw = 1; rw <= 8; ++rw) {
+    for (int d = 2; d <= 3; ++d) {
+      const houd_fn fn = d == 2 ? pick_houd<2>(rw) : pick_houd<3>(rw);
+      const cudaError_t e =
+          cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, cudaStream_t st) {
   HoudArgs ha;
-  ha.t_houd = t_houd;
   ha.RW = (jb.g.L0 + 31) / 32;
   ha.NBW = jb.g.R * ha.RW;
   const int in_smem = houdayer_smem(jb, 1);
@@ -437,8 +448,6 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t t_houd, uint3
   if (!ha.bitmaps_smem && !scratch) return cudaErrorInvalidValue;
   const int smem = houdayer_smem(jb, ha.bitmaps_smem);
   const houd_fn fn = jb.g.d == 2 ? pick_houd<2>(ha.RW) : pick_houd<3>(ha.RW);
-  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   fn<<<(unsigned)jb.S, HNT, (size_t)smem, st>>>(jb, dv, ha);
   return cudaGetLastError();
 }

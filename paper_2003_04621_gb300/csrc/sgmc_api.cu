@@ -3,6 +3,7 @@
 // (Metropolis thresholds, inverse temperatures) and the kernel launches.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -14,7 +15,7 @@ using namespace sgmc;
 namespace {
 
 struct Layout {
-  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, houd, houd_bytes, total;
+  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, gtab, esum, houd, houd_bytes, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -40,6 +41,7 @@ struct sg_handle {
   int wpc;         // 32-replica words per CTA of the packed resident kernel
   size_t smem;     // its dynamic shared memory
   bool fuse_pt;    // the exchange can run inside the resident kernel
+  bool global;     // sweeps stream the lattice from global memory (no resident kernel)
   int n_ctr;       // counters in the device array
 };
 
@@ -130,6 +132,9 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   L.ctr = take((size_t)(CTR_PT + T) * 8);
   L.meas_E = take(S * C * T * 4);
   L.meas_Q = take(S * T * 4);
+  // streaming sweep path: lane-pair threshold tables and per-replica bond sums
+  L.gtab = take(S * (size_t)jb.W * 256 * 8);
+  L.esum = take(S * (size_t)jb.W * 32 * 4);
   // Houdayer bitmaps that do not fit the kernel's shared-memory budget
   L.houd_bytes = 0;
   if (houdayer_possible(p, jb) && houdayer_smem(jb, 1) > HOUD_SMEM_BUDGET) L.houd_bytes = houdayer_scratch_bytes(jb);
@@ -148,6 +153,22 @@ int max_dyn_smem() {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
   return v;
+}
+
+// Once per device: allow the kernels the opt-in shared memory (outside any capture).
+std::mutex prep_mutex;
+bool prepared[64] = {false};
+cudaError_t prepare_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(prep_mutex);
+  if (dev < 64 && prepared[dev]) return cudaSuccess;
+  const int ms = max_dyn_smem();
+  e = prepare_resident_kernels(ms);
+  if (e == cudaSuccess) e = prepare_houdayer_kernels(ms);
+  if (e == cudaSuccess && dev < 64) prepared[dev] = true;
+  return e;
 }
 
 // Whether the packed resident kernel can run with this shape: the per-thread colour-1
@@ -202,36 +223,47 @@ sg_status check(sg_handle *h, cudaError_t e) {
 }
 
 template <bool FUSE, bool EONLY>
-sg_status launch_resident(sg_handle *h, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0, int n_mcs,
-                          int n_metro) {
+sg_status launch_resident(sg_handle *h, cudaStream_t st, int n_mcs, int n_metro) {
   return check(h, sgmc::launch_resident(h->job, h->dev, h->int8fmt != 0, h->nt, h->wpc, FUSE, EONLY, h->smem, st,
-                                        t_metro0, t_pt0, n_mcs, n_metro));
+                                        n_mcs, n_metro));
 }
 
 cudaStream_t as_stream(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
+uint2 *gtab_of(sg_handle *h) { return reinterpret_cast<uint2 *>(h->buf + h->lay.gtab); }
+uint32_t *esum_of(sg_handle *h) { return reinterpret_cast<uint32_t *>(h->buf + h->lay.esum); }
+
 sg_status sweeps(sg_handle *h, int n, cudaStream_t st) {
   if (n <= 0) return SG_OK;
-  sg_status r = launch_resident<false, false>(h, st, (uint32_t)h->t_metro, 0u, n, 1);
+  if (h->global) {
+    for (int a = 0; a < n; ++a) {
+      sg_status r = check(h, launch_global_sweep(h->job, h->dev, gtab_of(h), esum_of(h), st));
+      if (r != SG_OK) return r;
+      h->t_metro += 1;
+    }
+    return SG_OK;
+  }
+  sg_status r = launch_resident<false, false>(h, st, n, 1);
   if (r == SG_OK) h->t_metro += (uint64_t)n;
   return r;
 }
 
 sg_status exchange(sg_handle *h, cudaStream_t st) {
-  sg_status r = check(h, launch_exchange(h->job, h->dev, (uint32_t)h->t_pt, st));
+  sg_status r = check(h, launch_exchange(h->job, h->dev, st));
   if (r == SG_OK) h->t_pt += 1;
   return r;
 }
 
 sg_status recompute_energy(sg_handle *h, cudaStream_t st) {
-  return launch_resident<false, true>(h, st, 0u, 0u, 1, 1);
+  if (h->global) return check(h, launch_global_energy(h->job, h->dev, gtab_of(h), esum_of(h), st));
+  return launch_resident<false, true>(h, st, 1, 1);
 }
 
 // The cluster move itself (spins only; energies are stale until recomputed).
 sg_status houdayer_move(sg_handle *h, cudaStream_t st) {
   uint32_t *scratch = h->lay.houd_bytes ? reinterpret_cast<uint32_t *>(h->buf + h->lay.houd) : nullptr;
   const int limit = h->lay.houd_bytes ? 0 : HOUD_SMEM_BUDGET;
-  sg_status r = check(h, launch_houdayer(h->job, h->dev, (uint32_t)h->t_houd, scratch, limit, st));
+  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, limit, st));
   if (r == SG_OK) h->t_houd += 1;
   return r;
 }
@@ -286,11 +318,18 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   h->sticky = SG_OK;
   h->int8fmt = p->spin_format == SG_INT8;
   const int T = p->n_temps, d = p->ndim;
+  h->global = false;
   if (!choose_resident(h, max_dyn_smem())) {
-    delete h;
-    return SG_EUNSUPPORTED;
+    if (h->int8fmt) { // the int8 layout has no streaming path
+      delete h;
+      return SG_EUNSUPPORTED;
+    }
+    h->global = true; // the lattice does not fit a CTA: stream it from global memory
+    h->nt = 256;
+    h->wpc = 1;
+    h->smem = 0;
   }
-  h->fuse_pt = h->int8fmt ? true : (h->job.Wc == 1);
+  h->fuse_pt = !h->global && (h->int8fmt ? true : (h->job.Wc == 1));
   h->n_ctr = CTR_PT + T;
 
   h->beta.resize(T);
@@ -310,10 +349,13 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   dv.ctr = reinterpret_cast<unsigned long long *>(h->buf + h->lay.ctr);
 
   cudaStream_t st = as_stream(stream);
-  cudaError_t e = cudaMemcpyAsync(h->buf + h->lay.thr, h->thr.data(), h->thr.size() * 4, cudaMemcpyHostToDevice, st);
+  cudaError_t e = prepare_device();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->buf + h->lay.thr, h->thr.data(), h->thr.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->buf + h->lay.beta, h->beta.data(), h->beta.size() * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dv.ctr, 0, (size_t)h->n_ctr * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf + h->lay.esum, 0, (size_t)h->job.S * h->job.W * 32 * 4, st);
   if (e == cudaSuccess) e = launch_init(h->job, dv, h->int8fmt != 0, st);
   if (e != cudaSuccess) {
     delete h;
@@ -354,14 +396,14 @@ sg_status sg_houdayer(sg_handle *h, uintptr_t stream) {
   return r == SG_OK ? recompute_energy(h, st) : r;
 }
 
-sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
-  if (!h || n_mcs < 0) return SG_EINVAL;
-  if (h->sticky != SG_OK) return h->sticky;
+namespace {
+// Enqueue n_mcs Monte Carlo steps of one handle on `st` (Sec. 2.4 order) and advance
+// the host copies of its step counters.
+sg_status mcs_ops(sg_handle *h, int n_mcs, cudaStream_t st) {
   if (n_mcs == 0) return SG_OK;
-  cudaStream_t st = as_stream(stream);
   const int nm = h->p.n_metro;
-  if (!h->p.houdayer && h->fuse_pt) {
-    sg_status r = launch_resident<true, false>(h, st, (uint32_t)h->t_metro, (uint32_t)h->t_pt, n_mcs, nm);
+  if (!h->p.houdayer && h->fuse_pt && !h->global) {
+    sg_status r = launch_resident<true, false>(h, st, n_mcs, nm);
     if (r == SG_OK) {
       h->t_metro += (uint64_t)n_mcs * (uint64_t)nm;
       h->t_pt += (uint64_t)n_mcs;
@@ -373,9 +415,9 @@ sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
     sg_status r = sweeps(h, nm, st);
     if (r == SG_OK && h->p.houdayer) {
       r = houdayer_move(h, st);
-      if (r == SG_OK && h->fuse_pt) {
+      if (r == SG_OK && h->fuse_pt && !h->global) {
         // energies after the move, then the exchange, in one resident launch
-        r = launch_resident<true, true>(h, st, 0u, (uint32_t)h->t_pt, 1, 1);
+        r = launch_resident<true, true>(h, st, 1, 1);
         if (r == SG_OK) h->t_pt += 1;
         if (r != SG_OK) return r;
         continue;
@@ -387,6 +429,133 @@ sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
   }
   return SG_OK;
 }
+} // namespace
+
+sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream) {
+  if (!h || n_mcs < 0) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  return mcs_ops(h, n_mcs, as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------------
+// Batches: the MCS cycles of several jobs captured once into one CUDA graph, each job a
+// branch of its own (its kernels run concurrently with the other jobs'), replayed as
+// often as needed.  The kernels read their step counters on the device, so the same
+// graph serves every replay.
+// ---------------------------------------------------------------------------------
+struct sg_batch {
+  std::vector<sg_handle *> jobs;
+  cudaStream_t origin;               // capture stream (the legacy default stream cannot be captured)
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events; // fork + one join per job
+  int mcs_per_launch;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  std::vector<uint64_t> d_metro, d_pt, d_houd; // counter advance per replay, per job
+};
+
+void destroy_batch(sg_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  for (cudaStream_t q : b->streams) cudaStreamDestroy(q);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t mcs_per_launch, uintptr_t stream,
+                          sg_batch **out) {
+  if (!out || !handles || n_handles < 1 || mcs_per_launch < 1) return SG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n_handles; ++i) {
+    if (!handles[i]) return SG_EINVAL;
+    if (handles[i]->sticky != SG_OK) return handles[i]->sticky;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return SG_EINVAL;
+  }
+  sg_batch *b = new (std::nothrow) sg_batch();
+  if (!b) return SG_ENOMEM;
+  b->mcs_per_launch = mcs_per_launch;
+  b->graph = nullptr;
+  b->exec = nullptr;
+  b->origin = nullptr;
+  (void)stream; // nothing is enqueued here; sg_batch_run launches on its own stream
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  cudaStream_t origin = b->origin;
+  b->events.resize((size_t)n_handles + 1, nullptr);
+  for (auto &ev : b->events)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  b->streams.resize((size_t)n_handles, nullptr);
+  for (auto &q : b->streams)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    destroy_batch(b);
+    return SG_ECUDA;
+  }
+  // the kernels' shared-memory attributes were set when the handles were created, so the
+  // capture holds kernel launches and event edges only
+  e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    destroy_batch(b);
+    return SG_ECUDA;
+  }
+  sg_status r = SG_OK;
+  e = cudaEventRecord(b->events[0], origin);
+  for (int i = 0; i < n_handles && r == SG_OK && e == cudaSuccess; ++i) {
+    sg_handle *h = handles[i];
+    const uint64_t m0 = h->t_metro, p0 = h->t_pt, h0 = h->t_houd;
+    e = cudaStreamWaitEvent(b->streams[i], b->events[0], 0);
+    if (e == cudaSuccess) r = mcs_ops(h, mcs_per_launch, b->streams[i]);
+    // capture only records the work: the counters advance when the graph is launched
+    b->d_metro.push_back(h->t_metro - m0);
+    b->d_pt.push_back(h->t_pt - p0);
+    b->d_houd.push_back(h->t_houd - h0);
+    h->t_metro = m0;
+    h->t_pt = p0;
+    h->t_houd = h0;
+    if (e == cudaSuccess && r == SG_OK) e = cudaEventRecord(b->events[i + 1], b->streams[i]);
+    if (e == cudaSuccess && r == SG_OK) e = cudaStreamWaitEvent(origin, b->events[i + 1], 0);
+    b->jobs.push_back(h);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(origin, &g);
+  b->graph = g;
+  if (r != SG_OK || e != cudaSuccess || e2 != cudaSuccess || !g) {
+    for (sg_handle *h : b->jobs)
+      if (h->sticky == SG_ECUDA) h->sticky = SG_OK; // a failed capture leaves the jobs untouched
+    destroy_batch(b);
+    return r != SG_OK ? r : SG_ECUDA;
+  }
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    destroy_batch(b);
+    return SG_ECUDA;
+  }
+  *out = b;
+  return SG_OK;
+}
+
+sg_status sg_batch_run(sg_batch *b, int32_t n_launches, uintptr_t stream) {
+  if (!b || n_launches < 0) return SG_EINVAL;
+  for (sg_handle *h : b->jobs)
+    if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  for (int a = 0; a < n_launches; ++a) {
+    const cudaError_t e = cudaGraphLaunch(b->exec, st);
+    if (e != cudaSuccess) {
+      for (sg_handle *h : b->jobs) h->sticky = SG_ECUDA;
+      return SG_ECUDA;
+    }
+    for (size_t i = 0; i < b->jobs.size(); ++i) {
+      b->jobs[i]->t_metro += b->d_metro[i];
+      b->jobs[i]->t_pt += b->d_pt[i];
+      b->jobs[i]->t_houd += b->d_houd[i];
+    }
+  }
+  return SG_OK;
+}
+
+void sg_batch_destroy(sg_batch *b) { destroy_batch(b); }
 
 sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
   if (!h || !E_out) return SG_EINVAL;
@@ -487,20 +656,27 @@ sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out) {
 sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words) {
   if (!h) return SG_EINVAL;
   if (h->int8fmt) return (threads == 0 || threads == 256) && (words == 0 || words == 1) ? SG_OK : SG_EUNSUPPORTED;
+  if (words == -1) { // stream the lattice from global memory
+    h->global = true;
+    h->fuse_pt = false;
+    return SG_OK;
+  }
   const int nt = threads ? threads : h->nt;
-  const int wpc = words ? words : h->wpc;
+  const int wpc = words ? words : (h->global ? 1 : h->wpc);
   size_t sm = 0;
   if (!packed_shape_ok(h, nt, wpc, max_dyn_smem(), &sm)) return SG_EUNSUPPORTED;
   h->nt = nt;
   h->wpc = wpc;
   h->smem = sm;
+  h->global = false;
+  h->fuse_pt = h->job.Wc == 1;
   return SG_OK;
 }
 
 sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t *smem_bytes) {
   if (!h) return SG_EINVAL;
   if (threads) *threads = h->nt;
-  if (words) *words = h->wpc;
+  if (words) *words = h->global ? -1 : h->wpc;
   if (smem_bytes) *smem_bytes = (int32_t)h->smem;
   return SG_OK;
 }

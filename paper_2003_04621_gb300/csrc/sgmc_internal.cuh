@@ -30,7 +30,11 @@ constexpr int CTR_NEAR = 0;   // near-threshold exchange decisions
 constexpr int CTR_HSITES = 1; // sites flipped by Houdayer moves
 constexpr int CTR_ERROR = 2;  // bit flags of device-side errors (bounded waits that expired)
 constexpr int CTR_HMOVES = 3; // Houdayer moves with M > 0
-constexpr int CTR_PT = 4;     // [T-1] accepted exchanges per pair
+constexpr int CTR_TMETRO = 4; // Metropolis sweeps made (the t of the sweep counters)
+constexpr int CTR_TPT = 5;    // exchange passes made
+constexpr int CTR_THOUD = 6;  // Houdayer passes made
+constexpr int CTR_DONE = 7;   // finished-CTA ticket of the running kernel
+constexpr int CTR_PT = 8;     // [T-1] accepted exchanges per pair
 
 constexpr unsigned long long ERR_TMA_TIMEOUT = 1ull;
 constexpr unsigned long long ERR_HOUD_ROUNDS = 2ull; // a cluster fill hit its round limit (never expected)
@@ -94,6 +98,26 @@ __device__ __forceinline__ uint4 philox10(uint32_t x0, uint32_t x1, uint32_t x2,
     k1 += PH_W1;
   }
   return make_uint4(x0, x1, x2, x3);
+}
+
+// Step counters live on the device, so that any sequence of calls can be captured in a
+// CUDA graph and replayed: every kernel reads the counters it needs when it starts, and
+// the last CTA of the grid to finish (by an atomic ticket; every CTA has read the
+// counters before taking one) advances them.  Every CTA must call this exactly once.
+__device__ __forceinline__ void grid_done_advance(unsigned long long *ctr, unsigned long long d_metro,
+                                                  unsigned long long d_pt, unsigned long long d_houd) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long ticket = atomicAdd(&ctr[CTR_DONE], 1ull);
+    if (ticket == (unsigned long long)(gridDim.x * gridDim.y * gridDim.z) - 1ull) {
+      ctr[CTR_TMETRO] += d_metro;
+      ctr[CTR_TPT] += d_pt;
+      ctr[CTR_THOUD] += d_houd;
+      ctr[CTR_DONE] = 0ull;
+      __threadfence();
+    }
+  }
 }
 
 // Philox4x32-10 with the ten round keys given explicitly (kernel-parameter arrays).
@@ -260,13 +284,15 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 
 // Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
-                            bool energy_only, size_t smem, cudaStream_t st, uint32_t t_metro0, uint32_t t_pt0,
-                            int n_mcs, int n_metro);
-cudaError_t launch_exchange(const Job &jb, const Dev &dv, uint32_t t_pt, cudaStream_t st);
+                            bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro);
+cudaError_t launch_exchange(const Job &jb, const Dev &dv, cudaStream_t st);
+cudaError_t prepare_resident_kernels(int max_smem);
+cudaError_t prepare_houdayer_kernels(int max_smem);
+cudaError_t launch_global_sweep(const Job &jb, const Dev &dv, uint2 *tables, uint32_t *esum, cudaStream_t st);
+cudaError_t launch_global_energy(const Job &jb, const Dev &dv, uint2 *tables, uint32_t *esum, cudaStream_t st);
 int houdayer_smem(const Job &jb, int bitmaps_smem);
 size_t houdayer_scratch_bytes(const Job &jb);
-cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t t_houd, uint32_t *scratch, int smem_limit,
-                            cudaStream_t st);
+cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, cudaStream_t st);
 } // namespace sgmc
 
 namespace sgmc {

@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_run_mcs", "sg_measure",
     "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
-    "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_destroy", "sg_strerror",
+    "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
+    "sg_batch_run", "sg_batch_destroy", "sg_destroy", "sg_strerror",
 )
 
 _lib = None
@@ -85,6 +86,8 @@ def lib():
         "sg_thresholds": [P, P],
         "sg_set_launch": [P, I32, I32],
         "sg_get_launch": [P, P, P, P],
+        "sg_batch_create": [P, I32, I32, U, ctypes.POINTER(P)],
+        "sg_batch_run": [P, I32, U],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -92,6 +95,8 @@ def lib():
         fn.restype = ctypes.c_int
     L.sg_destroy.argtypes = [P]
     L.sg_destroy.restype = None
+    L.sg_batch_destroy.argtypes = [P]
+    L.sg_batch_destroy.restype = None
     L.sg_strerror.argtypes = [ctypes.c_int]
     L.sg_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -276,6 +281,36 @@ class Simulation:
         out = np.zeros((self.T, self.ndim), np.uint32)
         _check(lib().sg_thresholds(self._h, out.ctypes.data), "sg_thresholds")
         return out
+
+
+class Batch:
+    """Several simulations advanced together by one CUDA graph per launch (each job a
+    branch; see sg_batch_create).  Results equal those of running each job alone."""
+
+    def __init__(self, sims, mcs_per_launch: int = 1, stream=None):
+        self.sims = list(sims)
+        self.mcs_per_launch = int(mcs_per_launch)
+        self._stream = stream
+        arr = (ctypes.c_void_p * len(self.sims))(*[s_._h for s_ in self.sims])
+        b = ctypes.c_void_p()
+        _check(lib().sg_batch_create(arr, len(self.sims), self.mcs_per_launch, _stream_handle(stream),
+                                     ctypes.byref(b)), "sg_batch_create")
+        self._b = b
+
+    def run(self, n_launches: int = 1, stream=None):
+        _check(lib().sg_batch_run(self._b, int(n_launches), _stream_handle(stream if stream is not None
+                                                                             else self._stream)), "sg_batch_run")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().sg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w, stream=None, **overrides) -> Simulation:
