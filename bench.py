@@ -159,6 +159,91 @@ def run_reference(args, ws, rank):
     }))
 
 
+def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1):
+    """The uneven 3D batch (153 jobs of L = 8..32 and 16..48 temperatures) advanced
+    `mcs_per_launch` MCS per CUDA-graph launch: the jobs of one lattice size are swept by
+    one resident launch (a job table in the kernel's parameters), the five sizes run as
+    parallel branches.  Compared with the uniform L=16 job advanced the same number of MCS
+    per launch."""
+    import torch
+
+    from paper_2003_04621_gb300 import autotune
+    from paper_2003_04621_gb300.inputs import geometric_temps, workload_3d_l16, workload_batched_uneven
+    from paper_2003_04621_gb300.sgmc import Batch, Simulation
+
+    def mk(w):
+        return Simulation(w.ndim, w.dims, w.n_samples, w.n_chains, list(w.temps), coupling_seed=w.coupling_seed,
+                          sim_seed=w.sim_seed, sample_offset=w.sample_offset, stream=stream)
+
+    def timed(run, n):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        run(n)
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e)
+
+    jobs = workload_batched_uneven()
+    # the largest job of each lattice size leads its group: tune its shape, order it first
+    by_L = {}
+    for w in jobs:
+        by_L.setdefault(w.dims[0], []).append(w)
+    ordered, shapes = [], {}
+    for L, ws in by_L.items():
+        ws.sort(key=lambda w: -w.n_samples * w.T)
+        ordered.extend(ws)
+    sims = [mk(w) for w in ordered]
+    k = 0
+    for L, ws in by_L.items():
+        # tune the lattice size on a stand-in with the size's total samples and 32 temps
+        rep = Simulation(3, (L, L, L), sum(w.n_samples for w in ws), 2, geometric_temps(0.9, 2.0, 32), stream=stream)
+        autotune.tune(rep, stream=stream)
+        shapes[L] = rep.launch()
+        rep.close()
+        for s_ in sims[k:k + len(ws)]:
+            s_.set_launch(shapes[L]["threads"], shapes[L]["words"])
+        k += len(ws)
+    b = Batch(sims, mcs_per_launch=mcs_per_launch, stream=stream)
+    b.run(warmup, stream=stream)
+    ms = timed(lambda n: b.run(n, stream=stream), steps)
+    attempts = sum(w.attempts_per_sweep for w in jobs) * steps * mcs_per_launch
+    b.close()
+    for s_ in sims:
+        s_.close()
+    # the uniform single-size plain path, the same MCS per launch
+    u = workload_3d_l16()
+    us = mk(u)
+    autotune.tune(us, stream=stream)
+    us.run_mcs(mcs_per_launch, stream=stream)
+    ums = timed(lambda n: [us.run_mcs(mcs_per_launch, stream=stream) for _ in range(n)], steps)
+    uni = u.attempts_per_sweep * steps * mcs_per_launch / (ums * 1e6)
+    us.close()
+    value = attempts / (ms * 1e6)
+    return {"workload": "3D L in {8,12,16,24,32} x {2048,1024,512,128,32} samples, 16..48 temps per sample",
+            "jobs": len(jobs), "value": value, "unit": UNIT, "launches": steps, "mcs_per_launch": mcs_per_launch,
+            "ms_per_mcs": ms / (steps * mcs_per_launch), "uniform_plain_value": uni, "vs_uniform_plain": value / uni,
+            "shapes": {str(L): v for L, v in shapes.items()},
+            "launch": "per graph launch: one resident launch per lattice size (job table), sizes in parallel"}
+
+
+def bench_serving(n_jobs: int, rate: float = 50.0):
+    """Poisson(50/s, seed 7) stream of jobs served by continuous batching; p50/p99 latency."""
+    import torch
+
+    from paper_2003_04621_gb300.serve import Server, poisson_trace, summarize
+
+    free, _total = torch.cuda.mem_get_info()
+    arena = int(min(32 << 30, free // 3))
+    server = Server(arena_bytes=arena, quantum=100)
+    results = server.run(poisson_trace(n_jobs, rate=rate, seed=7))
+    out = summarize(results)
+    out.update({"rate_per_s": rate, "arena_gb": arena / 2**30, "quantum_mcs": 100,
+                "graph_builds": server.graph_builds, "graph_launches": server.graph_launches,
+                "trace": f"first {n_jobs} arrivals of the Poisson({rate}/s, seed 7) stream"})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,6 +251,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serve-jobs", type=int, default=20)
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -293,6 +380,9 @@ def main():
                           "peak_kind": pk_kind, "bytes_per_attempt": BYTES_PER_ATTEMPT},
         "e2e": e2e,
     }
+    if ws == 1 and not args.no_extras:
+        line["batched"] = bench_batched(stream, steps=max(4, args.steps // 8))
+        line["serving"] = bench_serving(args.serve_jobs)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         v, dt, done = cpu_baseline(w, cores, 40, cores)

@@ -20,6 +20,8 @@
 #include "sgmc_sweep.cuh"
 #include "sgmc_tma.cuh"
 
+#include <vector>
+
 namespace sgmc {
 
 // Expand the sample's coupling bit planes into one byte per site with the 2d bonds of
@@ -103,62 +105,71 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__re
   }
 }
 
-// Replica exchange of one chain from shared memory (Eq. 5), by one warp.  The lanes first
-// draw every pair's word u_k and turn the exact fp64 test into integer bounds on
-// dE = E_k - E_k+1 that are safe by a wide margin (see below); the sequential pass over
+// Replica exchange of one chain (T <= 64) from shared memory (Eq. 5), by one warp.  The
+// lanes first draw every pair's word u_k and turn the exact fp64 test into integer bounds
+// on dE = E_k - E_k+1 that are safe by a wide margin (see below); the sequential pass over
 // k = 0..T-2 then compares integers, and only a decision inside the margin (or u = 0)
 // takes the exact path with exp, identical to the standalone kernel and to the oracle.
 //
 // Bounds: with x = u 2^-32 and dbeta = beta_k - beta_k+1 > 0, delta = dbeta dE and the
 // exact rule "accept iff delta >= 0 or x < exp(delta)" is, for dE < 0, "dE > ln(x)/dbeta".
-// With theta = ln(x)/dbeta and margin mg = max(1e-6 (1 + |theta|), 1e-10/(dbeta x)):
-// dE >= theta + mg gives exp(delta) >= x exp(1e-10/x) >= x + 1e-10, and dE <= theta - mg
-// gives x - exp(delta) >= 5e-11, so both fast outcomes agree with the fp64 test and
-// are never within the 1e-12 near-threshold window, whatever the last-bit errors of
-// log, exp and the products.
+// With theta = ln(x)/dbeta and margin mg = max(4e-6 (1 + |theta|), 1e-10/(dbeta x)),
+// evaluated in fp32 (theta's error is below mg/8): dE >= theta + mg gives
+// exp(delta) >= x exp(1e-10/(2x)) >= x + 5e-11, and dE <= theta - mg gives
+// x - exp(delta) >= 2.5e-11, so both fast outcomes agree with the fp64 test and are
+// never within the 1e-12 near-threshold window, whatever the last-bit errors of exp and
+// the products.
 __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, int32_t *pm, int32_t *sl,
                                                     const int32_t *el, int32_t *accb, int32_t *rejb,
                                                     uint32_t *uw, unsigned int *pacc, unsigned int *pnear,
                                                     uint32_t *slowmask, uint32_t s_glob, uint32_t c, uint32_t t,
                                                     const Job &jb) {
   const int lane = threadIdx.x & 31;
-  if (lane + 1 < T) {
-    const int k = lane;
-    const uint32_t u = philox10_rk((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, jb.rk0, jb.rk1).x;
-    const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
-    bool slow = (u == 0u);
-    int A = 0, R = 0;
-    if (!slow) {
-      const double x = __dmul_rn((double)u, 0x1p-32);
-      const double theta = log(x) / dbeta;
-      const double mg = fmax(1e-6 * (1.0 + fabs(theta)), 1e-10 / (dbeta * x));
-      const double hi = theta + mg, lo = theta - mg;
-      const double LIM = 1073741824.0; // 2^30, beyond any |dE| <= 2 d N
-      if (!(hi == hi) || !(lo == lo)) {
-        slow = true;
-      } else {
-        A = hi >= LIM ? (int)LIM : (hi <= -LIM ? -(int)LIM : (int)ceil(hi));
-        R = lo <= -LIM ? -(int)LIM : (lo >= LIM ? (int)LIM : (int)floor(lo));
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int k = lane + 32 * half;
+    bool slow = false;
+    if (k + 1 < T) {
+      const uint32_t u = philox10_rk((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, jb.rk0, jb.rk1).x;
+      const float dbeta = (float)__dsub_rn(beta[k], beta[k + 1]);
+      slow = (u == 0u);
+      int A = 0, R = 0;
+      if (!slow) {
+        // bounds in fp32: ln x to ~3e-7 relative (log1p near x = 1, where 1 - x is exact),
+        // dbeta to 6e-8, so theta is within 5e-7 |theta| and the margin covers it 8 times
+        const float x = (float)u * 0x1p-32f;
+        const float lnx = u > 0x80000000u ? log1pf(-(float)(0u - u) * 0x1p-32f) : logf(x);
+        const float theta = lnx / dbeta;
+        const float mg = fmaxf(4e-6f * (1.0f + fabsf(theta)), 1e-10f / (dbeta * x));
+        const float hi = theta + mg, lo = theta - mg;
+        const float LIM = 1073741824.0f; // 2^30, beyond any |dE| <= 2 d N
+        if (!(hi == hi) || !(lo == lo)) {
+          slow = true;
+        } else {
+          A = hi >= LIM ? (int)LIM : (hi <= -LIM ? -(int)LIM : (int)ceilf(hi));
+          R = lo <= -LIM ? -(int)LIM : (lo >= LIM ? (int)LIM : (int)floorf(lo));
+        }
       }
+      accb[k] = A;
+      rejb[k] = R;
+      uw[k] = u;
     }
-    accb[k] = A;
-    rejb[k] = R;
-    uw[k] = u;
-    const uint32_t sm = __ballot_sync(__activemask(), slow);
-    if (lane == 0) *slowmask = sm;
+    const uint32_t sm = __ballot_sync(FULL, slow);
+    if (lane == 0) slowmask[half] = sm;
   }
   __syncwarp();
   if (lane == 0) {
-    const uint32_t slowm = T > 1 ? *slowmask : 0u;
+    const uint32_t slow0 = slowmask[0], slow1 = slowmask[1];
     for (int k = 0; k + 1 < T; ++k) {
       const int a = pm[k], b = pm[k + 1];
       const int dE = el[a] - el[b];
+      const bool slow = ((k < 32 ? (slow0 >> k) : (slow1 >> (k - 32))) & 1u) != 0u;
       bool accept;
       if (dE >= 0) {
         accept = true;
-      } else if (!((slowm >> k) & 1u) && dE >= accb[k]) {
+      } else if (!slow && dE >= accb[k]) {
         accept = true;
-      } else if (!((slowm >> k) & 1u) && dE <= rejb[k]) {
+      } else if (!slow && dE <= rejb[k]) {
         accept = false;
       } else {
         const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
@@ -180,10 +191,25 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
   __syncwarp();
 }
 
-template <int D, int NT, int WPC, bool FUSE_PT, bool ENERGY_ONLY>
-__global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT) k_resident_packed(Job jb, Dev dv, int n_mcs,
-                                                                               int n_metro) {
+// The resident kernel.  Each CTA is one item of one job: WPC consecutive 32-replica word
+// lattices of one sample (sample s, words w0 .. w0+WPC-1), staged in shared memory for
+// n_mcs MCS.  When the job's `fuse` flag is set the item holds whole chains (a chain is
+// Wc <= WPC words) and their exchange passes run between the MCS.  The job comes from a
+// table in parameter space, so one launch can sweep many jobs of one lattice shape.
+template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ>
+__global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
+    k_resident_packed(const __grid_constant__ ResidentParams<MAXJ> rp) {
   extern __shared__ __align__(128) unsigned char smem[];
+  int jsel = 0;
+  if (MAXJ > 1) {
+    for (int q = 1; q < rp.n_jobs; ++q)
+      if ((int)blockIdx.x >= rp.jobs[q].first_item) jsel = q;
+  }
+  const JobDesc &JD = rp.jobs[jsel];
+  const Job &jb = JD.jb;
+  const Dev &dv = JD.dv;
+  const bool fuse = JD.fuse != 0;
+  const int n_mcs = rp.n_mcs, n_metro = JD.n_metro;
   const Geo g = jb.g;
   const PackedSmem L = packed_smem(g.N, g.NW, D, NT, WPC);
   uint32_t *sp = reinterpret_cast<uint32_t *>(smem + L.spin);
@@ -193,26 +219,29 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT) k_resident_packed(J
   int32_t *epart = reinterpret_cast<int32_t *>(smem + L.epart);
   int32_t *ptw = reinterpret_cast<int32_t *>(smem + L.pt);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-  // per word w: pm, sl, el, pacc, accb, rejb, uw [32 each], then near and slow mask
-  auto PM = [&](int w) { return ptw + w * PT_WORDS; };
-  auto SL = [&](int w) { return ptw + w * PT_WORDS + 32; };
-  auto EL = [&](int w) { return ptw + w * PT_WORDS + 64; };
-  auto PACC = [&](int w) { return reinterpret_cast<unsigned int *>(ptw + w * PT_WORDS + 96); };
-  auto ACCB = [&](int w) { return ptw + w * PT_WORDS + 128; };
-  auto REJB = [&](int w) { return ptw + w * PT_WORDS + 160; };
-  auto UW = [&](int w) { return reinterpret_cast<uint32_t *>(ptw + w * PT_WORDS + 192); };
-  auto NEAR = [&](int w) { return reinterpret_cast<unsigned int *>(ptw + w * PT_WORDS + 224); };
-  auto SLOW = [&](int w) { return reinterpret_cast<uint32_t *>(ptw + w * PT_WORDS + 225); };
+  // per chain slot ci: pm, sl, el, pacc, accb, rejb, uw [64 each], then near and slow mask
+  auto PM = [&](int ci) { return ptw + ci * PT_WORDS; };
+  auto SL = [&](int ci) { return ptw + ci * PT_WORDS + 64; };
+  auto EL = [&](int ci) { return ptw + ci * PT_WORDS + 128; };
+  auto PACC = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 192); };
+  auto ACCB = [&](int ci) { return ptw + ci * PT_WORDS + 256; };
+  auto REJB = [&](int ci) { return ptw + ci * PT_WORDS + 320; };
+  auto UW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 384); };
+  auto NEAR = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 448); };
+  auto SLOW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 449); };
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const uint32_t t_metro0 = (uint32_t)dv.ctr[CTR_TMETRO], t_pt0 = (uint32_t)dv.ctr[CTR_TPT];
   const unsigned long long adv_metro = ENERGY_ONLY ? 0ull : (unsigned long long)n_mcs * n_metro;
-  const unsigned long long adv_pt = FUSE_PT ? (unsigned long long)n_mcs : 0ull;
+  const unsigned long long adv_pt = fuse ? (unsigned long long)n_mcs : 0ull;
   const int groups = jb.W / WPC;
-  const int s = blockIdx.x / groups;
-  const int w0 = (blockIdx.x - s * groups) * WPC;
+  const int li = (int)blockIdx.x - JD.first_item;
+  const int s = li / groups;
+  const int w0 = (li - s * groups) * WPC;
   const uint32_t s_glob = (uint32_t)(jb.s_off + s);
+  const int c0 = w0 / jb.Wc;              // first chain of the item
+  const int nch = fuse ? WPC / jb.Wc : 0; // whole chains held (fused exchange)
   int ngroups[WPC];
   uint32_t vmask[WPC], c3base[WPC];
 #pragma unroll
@@ -235,23 +264,24 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT) k_resident_packed(J
     bulk_g2s(sp, gsp, sbytes, bar);
     bulk_g2s(jpl, gj, jbytes, bar);
   }
-  // warp w < WPC owns word w0 + w: its chain, replicas and exchange
+  // warp w < WPC owns local word w: its chain slot, replica offset and valid lanes
   const int my_c = (w0 + warp) / jb.Wc;
   const int my_wc = (w0 + warp) - my_c * jb.Wc;
-  const int my_nvalid = min(32, jb.T - my_wc * 32);
+  const int my_ci = my_c - c0;
+  const int my_j0 = my_wc * 32;
+  const int my_nvalid = min(32, jb.T - my_j0);
   const size_t my_cb = ((size_t)s * jb.C + my_c) * jb.T;
-  if (warp < WPC) {
-    const int w = warp;
-    if (FUSE_PT) {
-      PM(w)[lane] = lane < jb.T ? dv.perm[my_cb + lane] : 0;
-      SL(w)[lane] = lane < jb.T ? dv.slot[my_cb + lane] : 0;
-      PACC(w)[lane] = 0u;
-      if (lane == 0) *NEAR(w) = 0u;
+  if (warp < nch) {
+    // warp ci loads chain ci's maps
+    const size_t cb = ((size_t)s * jb.C + c0 + warp) * jb.T;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      PM(warp)[j] = j < jb.T ? dv.perm[cb + j] : 0;
+      SL(warp)[j] = j < jb.T ? dv.slot[cb + j] : 0;
+      PACC(warp)[j] = 0u;
     }
-    if (!ENERGY_ONLY) {
-      const int kslot = lane < my_nvalid ? (FUSE_PT ? SL(w)[lane] : dv.slot[my_cb + my_wc * 32 + lane]) : 0;
-      fill_pair_table<D>(pair_tab + w * 256, lane, kslot, my_nvalid, dv.thr);
-    }
+    if (lane == 0) *NEAR(warp) = 0u;
   }
   const bool ok = mbar_wait(bar, 0, MBAR_MAX_TRIES);
   if (__syncthreads_or(!ok)) {
@@ -259,8 +289,12 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT) k_resident_packed(J
       atomicOr(&dv.ctr[CTR_ERROR], ERR_TMA_TIMEOUT);
       mbar_wait(bar, 0, MBAR_MAX_TRIES); // let copies still in flight land before exiting
     }
-    grid_done_advance(dv.ctr, adv_metro, adv_pt, 0ull);
+    job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, 0ull);
     return;
+  }
+  if (!ENERGY_ONLY && warp < WPC) {
+    const int kslot = lane < my_nvalid ? (fuse ? SL(my_ci)[my_j0 + lane] : dv.slot[my_cb + my_j0 + lane]) : 0;
+    fill_pair_table<D>(pair_tab + warp * 256, lane, kslot, my_nvalid, dv.thr);
   }
   expand_couplings<D, NT>(g, jpl, jbyte);
   __syncthreads();
@@ -287,41 +321,48 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT) k_resident_packed(J
       if (warp < WPC) {
         int32_t U = 0;
         for (int wq = 0; wq < NT / 32; ++wq) U += epart[warp * NT + wq * 32 + lane];
-        EL(warp)[lane] = 2 * U - D * g.N;
+        EL(my_ci)[my_j0 + lane] = 2 * U - D * g.N;
       }
-      if (!FUSE_PT || swp + 1 < n_inner) __syncthreads();
+      __syncthreads();
     }
-    if (FUSE_PT) {
-      // warp w exchanges chain w (one chain per word), then refreshes its lanes' thresholds
-      if (warp < WPC) {
-        const int w = warp;
-        __syncwarp();
-        exchange_chain_smem(jb.T, dv.beta, PM(w), SL(w), EL(w), ACCB(w), REJB(w), UW(w), PACC(w), NEAR(w),
-                            SLOW(w), s_glob, (uint32_t)my_c, t_pt0 + (uint32_t)m, jb);
-        if (!ENERGY_ONLY) fill_pair_table<D>(pair_tab + w * 256, lane, lane < my_nvalid ? SL(w)[lane] : 0, my_nvalid, dv.thr);
+    if (nch > 0) {
+      // warp ci exchanges chain ci, then refreshes the tables of the chain's words
+      if (warp < nch) {
+        exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), ACCB(warp), REJB(warp), UW(warp),
+                            PACC(warp), NEAR(warp), SLOW(warp), s_glob, (uint32_t)(c0 + warp),
+                            t_pt0 + (uint32_t)m, jb);
+        if (!ENERGY_ONLY) {
+          for (int wc = 0; wc < jb.Wc; ++wc) {
+            const int nv = min(32, jb.T - wc * 32);
+            fill_pair_table<D>(pair_tab + (warp * jb.Wc + wc) * 256, lane,
+                               lane < nv ? SL(warp)[wc * 32 + lane] : 0, nv, dv.thr);
+          }
+        }
       }
       __syncthreads();
     }
   }
 
-  if (warp < WPC) {
-    const int w = warp;
-    if (lane < my_nvalid) dv.E[my_cb + my_wc * 32 + lane] = EL(w)[lane];
-    if (FUSE_PT) {
-      if (lane < jb.T) {
-        dv.perm[my_cb + lane] = PM(w)[lane];
-        dv.slot[my_cb + lane] = SL(w)[lane];
+  if (warp < WPC && lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = EL(my_ci)[my_j0 + lane];
+  if (warp < nch) {
+    const size_t cb = ((size_t)s * jb.C + c0 + warp) * jb.T;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      if (j < jb.T) {
+        dv.perm[cb + j] = PM(warp)[j];
+        dv.slot[cb + j] = SL(warp)[j];
       }
-      if (lane + 1 < jb.T && PACC(w)[lane]) atomicAdd(&dv.ctr[CTR_PT + lane], (unsigned long long)PACC(w)[lane]);
-      if (lane == 0 && *NEAR(w)) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*NEAR(w));
+      if (j + 1 < jb.T && PACC(warp)[j]) atomicAdd(&dv.ctr[CTR_PT + j], (unsigned long long)PACC(warp)[j]);
     }
+    if (lane == 0 && *NEAR(warp)) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*NEAR(warp));
   }
   if (!ENERGY_ONLY) {
     fence_proxy_async(); // this thread's shared-memory writes -> visible to the TMA store
     __syncthreads();
     if (tid == 0) bulk_s2g_and_wait(gsp, sp, 4u * (uint32_t)(g.N * WPC));
   }
-  grid_done_advance(dv.ctr, adv_metro, adv_pt, 0ull);
+  job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, 0ull);
 }
 
 // ---------------------------------------------------------------------------------
@@ -513,83 +554,148 @@ __global__ void k_exchange(Job jb, Dev dv) {
 }
 
 namespace {
-typedef void (*resident_fn)(Job, Dev, int, int);
-
-template <int D, int WPC, bool FUSE, bool EONLY>
-resident_fn pick_packed_nt(int nt) {
-  switch (nt) {
-  case 128: return k_resident_packed<D, 128, WPC, FUSE, EONLY>;
-  case 256: return k_resident_packed<D, 256, WPC, FUSE, EONLY>;
-  case 512: return k_resident_packed<D, 512, WPC, FUSE, EONLY>;
-  default: return k_resident_packed<D, 1024, WPC, FUSE, EONLY>;
-  }
-}
+typedef void (*int8_fn)(Job, Dev, int, int);
 
 template <bool FUSE, bool EONLY>
-resident_fn pick_packed(int d, int nt, int wpc) {
-  if (d == 2) return wpc == 2 ? pick_packed_nt<2, 2, FUSE, EONLY>(nt) : pick_packed_nt<2, 1, FUSE, EONLY>(nt);
-  return wpc == 2 ? pick_packed_nt<3, 2, FUSE, EONLY>(nt) : pick_packed_nt<3, 1, FUSE, EONLY>(nt);
-}
-
-template <bool FUSE, bool EONLY>
-resident_fn pick_int8(int d) {
+int8_fn pick_int8(int d) {
   return d == 2 ? k_resident_int8<2, 256, FUSE, EONLY> : k_resident_int8<3, 256, FUSE, EONLY>;
 }
 
-template <bool FUSE, bool EONLY>
-resident_fn pick(bool int8fmt, int d, int nt, int wpc) {
-  return int8fmt ? pick_int8<FUSE, EONLY>(d) : pick_packed<FUSE, EONLY>(d, nt, wpc);
+template <int MAXJ>
+using packed_fn = void (*)(ResidentParams<MAXJ>);
+
+template <int D, int WPC, bool EONLY, int MAXJ>
+packed_fn<MAXJ> pick_packed_nt(int nt) {
+  switch (nt) {
+  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ>;
+  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ>;
+  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ>;
+  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ>;
+  }
+}
+
+template <bool EONLY, int MAXJ>
+packed_fn<MAXJ> pick_packed(int d, int nt, int wpc) {
+  if (d == 2) return wpc == 2 ? pick_packed_nt<2, 2, EONLY, MAXJ>(nt) : pick_packed_nt<2, 1, EONLY, MAXJ>(nt);
+  return wpc == 2 ? pick_packed_nt<3, 2, EONLY, MAXJ>(nt) : pick_packed_nt<3, 1, EONLY, MAXJ>(nt);
 }
 } // namespace
 
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro) {
-  resident_fn fn;
-  if (energy_only && fuse_pt) fn = pick<true, true>(int8fmt, jb.g.d, nthreads, wpc);
-  else if (energy_only) fn = pick<false, true>(int8fmt, jb.g.d, nthreads, wpc);
-  else if (fuse_pt) fn = pick<true, false>(int8fmt, jb.g.d, nthreads, wpc);
-  else fn = pick<false, false>(int8fmt, jb.g.d, nthreads, wpc);
   if (int8fmt) {
-    nthreads = 256;
-    wpc = 1;
+    int8_fn fn;
+    if (energy_only && fuse_pt) fn = pick_int8<true, true>(jb.g.d);
+    else if (energy_only) fn = pick_int8<false, true>(jb.g.d);
+    else if (fuse_pt) fn = pick_int8<true, false>(jb.g.d);
+    else fn = pick_int8<false, false>(jb.g.d);
+    fn<<<(unsigned)(jb.S * jb.C), 256, smem, st>>>(jb, dv, n_mcs, n_metro);
+    return cudaGetLastError();
   }
-  const unsigned grid = int8fmt ? (unsigned)(jb.S * jb.C) : (unsigned)(jb.S * (jb.W / wpc));
-  fn<<<grid, nthreads, smem, st>>>(jb, dv, n_mcs, n_metro);
+  ResidentParams<1> rp;
+  rp.n_jobs = 1;
+  rp.n_mcs = n_mcs;
+  rp.pad0 = rp.pad1 = 0;
+  rp.jobs[0].jb = jb;
+  rp.jobs[0].dv = dv;
+  rp.jobs[0].first_item = 0;
+  rp.jobs[0].n_items = jb.S * (jb.W / wpc);
+  rp.jobs[0].fuse = fuse_pt ? 1 : 0;
+  rp.jobs[0].n_metro = n_metro;
+  const packed_fn<1> fn = energy_only ? pick_packed<true, 1>(jb.g.d, nthreads, wpc)
+                                      : pick_packed<false, 1>(jb.g.d, nthreads, wpc);
+  fn<<<(unsigned)rp.jobs[0].n_items, nthreads, smem, st>>>(rp);
   return cudaGetLastError();
+}
+
+cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int wpc, size_t smem, cudaStream_t st,
+                                  int n_mcs) {
+  for (int base = 0; base < n_jobs; base += MAX_BATCH_JOBS) {
+    const int n = n_jobs - base < MAX_BATCH_JOBS ? n_jobs - base : MAX_BATCH_JOBS;
+    std::vector<char> raw(sizeof(ResidentParams<MAX_BATCH_JOBS>));
+    ResidentParams<MAX_BATCH_JOBS> &rp = *reinterpret_cast<ResidentParams<MAX_BATCH_JOBS> *>(raw.data());
+    rp.n_jobs = n;
+    rp.n_mcs = n_mcs;
+    rp.pad0 = rp.pad1 = 0;
+    int items = 0;
+    for (int i = 0; i < n; ++i) {
+      rp.jobs[i] = jobs[base + i];
+      rp.jobs[i].first_item = items;
+      items += rp.jobs[i].n_items;
+    }
+    const packed_fn<MAX_BATCH_JOBS> fn = pick_packed<false, MAX_BATCH_JOBS>(jobs[base].jb.g.d, nthreads, wpc);
+    fn<<<(unsigned)items, nthreads, smem, st>>>(rp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Allow every resident kernel the device's full opt-in shared memory (the attribute only
 // caps what a launch may request; it does not change occupancy).  Not a stream operation,
 // so it is done once per device before any launch or capture.
 cudaError_t prepare_resident_kernels(int max_smem) {
-  const resident_fn fns[] = {
-      pick<false, false>(false, 2, 128, 1), pick<false, false>(false, 2, 256, 1), pick<false, false>(false, 2, 512, 1),
-      pick<false, false>(false, 2, 1024, 1), pick<false, false>(false, 2, 128, 2), pick<false, false>(false, 2, 256, 2),
-      pick<false, false>(false, 2, 512, 2), pick<false, false>(false, 2, 1024, 2), pick<false, false>(false, 3, 128, 1),
-      pick<false, false>(false, 3, 256, 1), pick<false, false>(false, 3, 512, 1), pick<false, false>(false, 3, 1024, 1),
-      pick<false, false>(false, 3, 128, 2), pick<false, false>(false, 3, 256, 2), pick<false, false>(false, 3, 512, 2),
-      pick<false, false>(false, 3, 1024, 2), pick<true, false>(false, 2, 128, 1), pick<true, false>(false, 2, 256, 1),
-      pick<true, false>(false, 2, 512, 1), pick<true, false>(false, 2, 1024, 1), pick<true, false>(false, 2, 128, 2),
-      pick<true, false>(false, 2, 256, 2), pick<true, false>(false, 2, 512, 2), pick<true, false>(false, 2, 1024, 2),
-      pick<true, false>(false, 3, 128, 1), pick<true, false>(false, 3, 256, 1), pick<true, false>(false, 3, 512, 1),
-      pick<true, false>(false, 3, 1024, 1), pick<true, false>(false, 3, 128, 2), pick<true, false>(false, 3, 256, 2),
-      pick<true, false>(false, 3, 512, 2), pick<true, false>(false, 3, 1024, 2), pick<false, true>(false, 2, 128, 1),
-      pick<false, true>(false, 2, 256, 1), pick<false, true>(false, 2, 512, 1), pick<false, true>(false, 2, 1024, 1),
-      pick<false, true>(false, 2, 128, 2), pick<false, true>(false, 2, 256, 2), pick<false, true>(false, 2, 512, 2),
-      pick<false, true>(false, 2, 1024, 2), pick<false, true>(false, 3, 128, 1), pick<false, true>(false, 3, 256, 1),
-      pick<false, true>(false, 3, 512, 1), pick<false, true>(false, 3, 1024, 1), pick<false, true>(false, 3, 128, 2),
-      pick<false, true>(false, 3, 256, 2), pick<false, true>(false, 3, 512, 2), pick<false, true>(false, 3, 1024, 2),
-      pick<true, true>(false, 2, 128, 1), pick<true, true>(false, 2, 256, 1), pick<true, true>(false, 2, 512, 1),
-      pick<true, true>(false, 2, 1024, 1), pick<true, true>(false, 2, 128, 2), pick<true, true>(false, 2, 256, 2),
-      pick<true, true>(false, 2, 512, 2), pick<true, true>(false, 2, 1024, 2), pick<true, true>(false, 3, 128, 1),
-      pick<true, true>(false, 3, 256, 1), pick<true, true>(false, 3, 512, 1), pick<true, true>(false, 3, 1024, 1),
-      pick<true, true>(false, 3, 128, 2), pick<true, true>(false, 3, 256, 2), pick<true, true>(false, 3, 512, 2),
-      pick<true, true>(false, 3, 1024, 2), pick<false, false>(true, 2, 256, 1), pick<false, false>(true, 3, 256, 1),
-      pick<true, false>(true, 2, 256, 1), pick<true, false>(true, 3, 256, 1), pick<false, true>(true, 2, 256, 1),
-      pick<false, true>(true, 3, 256, 1), pick<true, true>(true, 2, 256, 1), pick<true, true>(true, 3, 256, 1)};
-  for (resident_fn fn : fns) {
-    const cudaError_t e =
-        cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  std::vector<const void *> fns;
+  for (int d = 2; d <= 3; ++d)
+    for (int nt : {128, 256, 512, 1024})
+      for (int wpc = 1; wpc <= 2; ++wpc) {
+        fns.push_back((const void *)pick_packed<false, 1>(d, nt, wpc));
+        fns.push_back((const void *)pick_packed<true, 1>(d, nt, wpc));
+        fns.push_back((const void *)pick_packed<false, MAX_BATCH_JOBS>(d, nt, wpc));
+      }
+  for (int d = 2; d <= 3; ++d) {
+    fns.push_back((const void *)pick_int8<false, false>(d));
+    fns.push_back((const void *)pick_int8<true, false>(d));
+    fns.push_back((const void *)pick_int8<false, true>(d));
+    fns.push_back((const void *)pick_int8<true, true>(d));
+  }
+  for (const void *fn : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Exchange passes of many jobs in one launch: CTAs [first_item, first_item + n_items) of
+// the grid belong to job j (128 chains per CTA), one thread per (sample, chain).
+__global__ void k_exchange_batch(const __grid_constant__ ResidentParams<MAX_BATCH_JOBS> rp) {
+  int jsel = 0;
+  for (int q = 1; q < rp.n_jobs; ++q)
+    if ((int)blockIdx.x >= rp.jobs[q].first_item) jsel = q;
+  const JobDesc &JD = rp.jobs[jsel];
+  const Job &jb = JD.jb;
+  const Dev &dv = JD.dv;
+  const int chain = ((int)blockIdx.x - JD.first_item) * blockDim.x + threadIdx.x;
+  const uint32_t t_pt = (uint32_t)dv.ctr[CTR_TPT];
+  if (chain < jb.S * jb.C) {
+    const int s = chain / jb.C;
+    const int c = chain - s * jb.C;
+    const size_t base = (size_t)chain * jb.T;
+    unsigned long long *ctr = dv.ctr;
+    exchange_chain(jb.T, dv.beta, dv.perm + base, dv.slot + base, dv.E + base, (uint32_t)(jb.s_off + s),
+                   (uint32_t)c, t_pt, jb.sk0, jb.sk1, [&](int k) { atomicAdd(&ctr[CTR_PT + k], 1ull); },
+                   [&]() { atomicAdd(&ctr[CTR_NEAR], 1ull); });
+  }
+  job_done_advance(dv.ctr, JD.n_items, 0ull, 1ull, 0ull);
+}
+
+cudaError_t launch_exchange_batch(JobDesc *jobs, int n_jobs, cudaStream_t st) {
+  for (int base = 0; base < n_jobs; base += MAX_BATCH_JOBS) {
+    const int n = n_jobs - base < MAX_BATCH_JOBS ? n_jobs - base : MAX_BATCH_JOBS;
+    std::vector<char> raw(sizeof(ResidentParams<MAX_BATCH_JOBS>));
+    ResidentParams<MAX_BATCH_JOBS> &rp = *reinterpret_cast<ResidentParams<MAX_BATCH_JOBS> *>(raw.data());
+    rp.n_jobs = n;
+    rp.n_mcs = 1;
+    rp.pad0 = rp.pad1 = 0;
+    int ctas = 0;
+    for (int i = 0; i < n; ++i) {
+      rp.jobs[i] = jobs[base + i];
+      rp.jobs[i].first_item = ctas;
+      rp.jobs[i].n_items = (jobs[base + i].jb.S * jobs[base + i].jb.C + 127) / 128;
+      ctas += rp.jobs[i].n_items;
+    }
+    k_exchange_batch<<<(unsigned)ctas, 128, 0, st>>>(rp);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -329,7 +329,7 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
     h->wpc = 1;
     h->smem = 0;
   }
-  h->fuse_pt = !h->global && (h->int8fmt ? true : (h->job.Wc == 1));
+  h->fuse_pt = !h->global && (h->int8fmt ? true : (h->wpc % h->job.Wc == 0));
   h->n_ctr = CTR_PT + T;
 
   h->beta.resize(T);
@@ -502,21 +502,98 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
   }
   sg_status r = SG_OK;
   e = cudaEventRecord(b->events[0], origin);
+  // jobs that the multi-job resident kernel can sweep together: packed spins, resident,
+  // no Houdayer move; grouped by lattice shape and words per chain (one launch per group
+  // and MCS chunk)
+  std::vector<int> group_of((size_t)n_handles, -1);
+  std::vector<std::vector<int>> groups;
+  for (int i = 0; i < n_handles; ++i) {
+    const sg_handle *h = handles[i];
+    if (h->int8fmt || h->global || h->p.houdayer) continue;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const sg_handle *o = handles[groups[gi][0]];
+      if (o->job.g.d == h->job.g.d && o->job.g.L0 == h->job.g.L0 && o->job.g.L1 == h->job.g.L1 &&
+          o->job.g.L2 == h->job.g.L2 && o->job.Wc == h->job.Wc) {
+        group_of[i] = (int)gi;
+        groups[gi].push_back(i);
+        break;
+      }
+    }
+    if (group_of[i] < 0) {
+      group_of[i] = (int)groups.size();
+      groups.push_back({i});
+    }
+  }
+  for (int i = 0; i < n_handles; ++i) b->jobs.push_back(handles[i]);
+  std::vector<uint64_t> m0, p0, h0;
+  for (sg_handle *h : b->jobs) {
+    m0.push_back(h->t_metro);
+    p0.push_back(h->t_pt);
+    h0.push_back(h->t_houd);
+  }
+  const int smem_limit = max_dyn_smem();
+  for (size_t gi = 0; gi < groups.size() && r == SG_OK && e == cudaSuccess; ++gi) {
+    cudaStream_t q = b->streams[groups[gi][0]];
+    e = cudaStreamWaitEvent(q, b->events[0], 0);
+    // one shape for the group: the first job's (tuned) shape, falling back to one word
+    // per CTA when a job has an odd number of words or two do not fit
+    sg_handle *lead = handles[groups[gi][0]];
+    int wpc = lead->wpc;
+    size_t sm = 0;
+    for (int i : groups[gi])
+      if (handles[i]->job.W % wpc) wpc = 1;
+    if (wpc == 2 && !packed_shape_ok(lead, lead->nt, 2, smem_limit, &sm)) wpc = 1;
+    if (!packed_shape_ok(lead, lead->nt, wpc, smem_limit, &sm)) {
+      r = SG_EUNSUPPORTED;
+      break;
+    }
+    std::vector<JobDesc> descs;
+    std::vector<sg_handle *> unfused;
+    for (int i : groups[gi]) {
+      sg_handle *h = handles[i];
+      JobDesc jd;
+      jd.jb = h->job;
+      jd.dv = h->dev;
+      jd.first_item = 0;
+      jd.n_items = h->job.S * (h->job.W / wpc);
+      jd.fuse = (wpc % h->job.Wc == 0) ? 1 : 0;
+      jd.n_metro = h->p.n_metro;
+      descs.push_back(jd);
+      if (!jd.fuse) unfused.push_back(h);
+    }
+    // a group is fused or not as a whole (same lattice and words per chain): fused groups
+    // run the whole chunk in one launch, the others alternate sweeps and one exchange
+    // launch for all their jobs
+    const int chunk = unfused.empty() ? mcs_per_launch : 1;
+    for (int m = 0; m < mcs_per_launch && e == cudaSuccess; m += chunk) {
+      e = launch_resident_batch(descs.data(), (int)descs.size(), lead->nt, wpc, sm, q, chunk);
+      if (e == cudaSuccess && !unfused.empty()) e = launch_exchange_batch(descs.data(), (int)descs.size(), q);
+    }
+    for (int i : groups[gi]) {
+      sg_handle *h = handles[i];
+      h->t_metro += (uint64_t)mcs_per_launch * (uint64_t)h->p.n_metro;
+      h->t_pt += (uint64_t)mcs_per_launch;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->events[groups[gi][0] + 1], q);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, b->events[groups[gi][0] + 1], 0);
+  }
   for (int i = 0; i < n_handles && r == SG_OK && e == cudaSuccess; ++i) {
+    if (group_of[i] >= 0) continue;
     sg_handle *h = handles[i];
-    const uint64_t m0 = h->t_metro, p0 = h->t_pt, h0 = h->t_houd;
     e = cudaStreamWaitEvent(b->streams[i], b->events[0], 0);
     if (e == cudaSuccess) r = mcs_ops(h, mcs_per_launch, b->streams[i]);
-    // capture only records the work: the counters advance when the graph is launched
-    b->d_metro.push_back(h->t_metro - m0);
-    b->d_pt.push_back(h->t_pt - p0);
-    b->d_houd.push_back(h->t_houd - h0);
-    h->t_metro = m0;
-    h->t_pt = p0;
-    h->t_houd = h0;
     if (e == cudaSuccess && r == SG_OK) e = cudaEventRecord(b->events[i + 1], b->streams[i]);
     if (e == cudaSuccess && r == SG_OK) e = cudaStreamWaitEvent(origin, b->events[i + 1], 0);
-    b->jobs.push_back(h);
+  }
+  // capture only records the work: the counters advance when the graph is launched
+  for (size_t i = 0; i < b->jobs.size(); ++i) {
+    sg_handle *h = b->jobs[i];
+    b->d_metro.push_back(h->t_metro - m0[i]);
+    b->d_pt.push_back(h->t_pt - p0[i]);
+    b->d_houd.push_back(h->t_houd - h0[i]);
+    h->t_metro = m0[i];
+    h->t_pt = p0[i];
+    h->t_houd = h0[i];
   }
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(origin, &g);
@@ -669,7 +746,7 @@ sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words) {
   h->wpc = wpc;
   h->smem = sm;
   h->global = false;
-  h->fuse_pt = h->job.Wc == 1;
+  h->fuse_pt = wpc % h->job.Wc == 0;
   return SG_OK;
 }
 

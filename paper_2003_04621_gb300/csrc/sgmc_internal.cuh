@@ -74,6 +74,28 @@ struct Dev {
   unsigned long long *ctr;
 };
 
+// One job of a resident-kernel launch: its description, the CTAs it owns (a contiguous
+// range of the grid), whether its exchange runs inside the kernel, and its sweeps per MCS.
+struct JobDesc {
+  Job jb;
+  Dev dv;
+  int first_item; // first CTA of this job
+  int n_items;    // CTAs of this job
+  int fuse;       // 1: every CTA holds whole chains and runs their exchange between MCS
+  int n_metro;    // sweeps per MCS
+};
+
+// Kernel parameters of the resident kernel: up to MAXJ jobs of one lattice shape.  The
+// table lives in the kernel's parameter space (read through constant memory).
+template <int MAXJ>
+struct ResidentParams {
+  int n_jobs;
+  int n_mcs;
+  int pad0, pad1;
+  JobDesc jobs[MAXJ];
+};
+constexpr int MAX_BATCH_JOBS = 96;
+
 // ---------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64
 // multiplies; the new state is (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0); the key is
@@ -98,6 +120,23 @@ __device__ __forceinline__ uint4 philox10(uint32_t x0, uint32_t x1, uint32_t x2,
     k1 += PH_W1;
   }
   return make_uint4(x0, x1, x2, x3);
+}
+
+// As grid_done_advance, for the `n_items` CTAs of one job inside a larger grid.
+__device__ __forceinline__ void job_done_advance(unsigned long long *ctr, int n_items, unsigned long long d_metro,
+                                                 unsigned long long d_pt, unsigned long long d_houd) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long ticket = atomicAdd(&ctr[CTR_DONE], 1ull);
+    if (ticket == (unsigned long long)n_items - 1ull) {
+      ctr[CTR_TMETRO] += d_metro;
+      ctr[CTR_TPT] += d_pt;
+      ctr[CTR_THOUD] += d_houd;
+      ctr[CTR_DONE] = 0ull;
+      __threadfence();
+    }
+  }
 }
 
 // Step counters live on the device, so that any sequence of calls can be captured in a
@@ -245,7 +284,7 @@ __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 // Shared-memory map of the resident packed kernel: `wpc` 32-replica word lattices of one
 // sample, its expanded couplings, per-lane threshold tables, energy partial sums and the
 // per-chain exchange scratch.
-constexpr int PT_WORDS = 7 * 32 + 4; // per word: perm, slot, E, accepts, accept/reject bounds, u; flags
+constexpr int PT_WORDS = 7 * 64 + 4; // per chain (<= 64 replicas): perm, slot, E, accepts, bounds, u; flags
 struct PackedSmem {
   int spin, jbyte, jpl, thr, epart, pt, bar, total;
 };
@@ -285,7 +324,12 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 // Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro);
+// Several jobs of the same lattice shape in one launch (chunks of MAX_BATCH_JOBS).
+// jobs[i].n_items/fuse/n_metro must be filled; first_item is set here.
+cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int wpc, size_t smem, cudaStream_t st,
+                                  int n_mcs);
 cudaError_t launch_exchange(const Job &jb, const Dev &dv, cudaStream_t st);
+cudaError_t launch_exchange_batch(JobDesc *jobs, int n_jobs, cudaStream_t st);
 cudaError_t prepare_resident_kernels(int max_smem);
 cudaError_t prepare_houdayer_kernels(int max_smem);
 cudaError_t launch_global_sweep(const Job &jb, const Dev &dv, uint2 *tables, uint32_t *esum, cudaStream_t st);

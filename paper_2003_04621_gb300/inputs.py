@@ -100,3 +100,24 @@ def workload_2d_l128_houdayer() -> Workload:
     Metropolis + Houdayer + PT each MCS, 5000 MCS."""
     return Workload("2d_L128_S256_T24_houdayer", 2, (128, 128), 256, 2,
                     geometric_temps(0.2, 1.6, 24), houdayer=True, n_mcs=5000)
+
+
+def workload_batched_uneven(seed: int = 1, n_mcs: int = 2000) -> List[Workload]:
+    """3D +-J batches of uneven size: L = 8, 12, 16, 24, 32 with 2048, 1024, 512, 128 and 32
+    samples; each sample draws its number of temperatures uniformly in 16..48 (MT19937,
+    `seed`), geometric in [0.9, 2.0].  Samples of equal (L, T) form one job; a job's
+    samples are numbered consecutively after those of the same L with fewer temperatures,
+    and that number is the sample's job-wide index (its random keys)."""
+    import numpy as np
+
+    rng = np.random.Generator(np.random.MT19937(seed))
+    jobs = []
+    for L, S in ((8, 2048), (12, 1024), (16, 512), (24, 128), (32, 32)):
+        Ts = rng.integers(16, 49, size=S)
+        base = 0
+        for T in sorted(set(int(x) for x in Ts)):
+            count = int((Ts == T).sum())
+            jobs.append(Workload(f"3d_L{L}_T{T}", 3, (L, L, L), count, 2, geometric_temps(0.9, 2.0, T),
+                                 sample_offset=base, n_mcs=n_mcs))
+            base += count
+    return jobs

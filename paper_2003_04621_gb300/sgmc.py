@@ -150,7 +150,10 @@ class Simulation:
     """One simulation job on the current CUDA device (see ``include/sgmc.h``)."""
 
     def __init__(self, ndim, dims, n_samples, n_chains, temps, coupling_seed=1, sim_seed=1, p_plus=0.5,
-                 spin_format="packed", houdayer=False, n_metro=1, sample_offset=0, stream=None, device=None):
+                 spin_format="packed", houdayer=False, n_metro=1, sample_offset=0, stream=None, device=None,
+                 device_buffer=None):
+        """device_buffer: optional (device pointer, bytes) the job lives in (256-byte
+        aligned, at least query_bytes); by default a torch buffer is allocated."""
         import torch
 
         L = lib()
@@ -163,10 +166,16 @@ class Simulation:
         self.params, self._temps = make_params(ndim, dims, n_samples, n_chains, temps, coupling_seed, sim_seed,
                                                p_plus, spin_format, houdayer, n_metro, sample_offset)
         self.bytes = query_bytes(self.params)
-        # 256-byte alignment: over-allocate and offset (torch's allocator aligns further anyway)
-        self._buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
-        base = self._buf.data_ptr()
-        self._ptr = (base + 255) & ~255
+        if device_buffer is not None:
+            self._buf = None
+            self._ptr, nbytes = int(device_buffer[0]), int(device_buffer[1])
+            if self._ptr & 255 or nbytes < self.bytes:
+                raise ValueError("device_buffer must be 256-byte aligned and hold query_bytes() bytes")
+        else:
+            # 256-byte alignment: over-allocate and offset
+            self._buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+            base = self._buf.data_ptr()
+            self._ptr = (base + 255) & ~255
         self._stream = stream
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

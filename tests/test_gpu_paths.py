@@ -92,3 +92,26 @@ def test_batch_equals_jobs_run_alone(oracle_mod):
     for a, s in zip(alone, batched):
         assert (a.spins() == s.spins()).all()
     b.close()
+
+
+def test_batch_of_one_lattice_many_temperature_counts(oracle_mod):
+    """Jobs sharing one lattice shape are swept by ONE resident launch per MCS chunk (a
+    job table in the kernel's parameters), including chains of 33..48 replicas exchanged
+    inside the kernel; a one-chain job forces one word per CTA for its group."""
+    from paper_2003_04621_gb300.sgmc import Batch
+
+    dims = (8, 6, 8)
+    specs = [dict(ndim=3, dims=dims, n_samples=S, n_chains=2, temps=geometric_temps(0.9, 2.0, T), sim_seed=7,
+                  sample_offset=off)
+             for S, T, off in ((5, 12, 0), (3, 20, 5), (2, 33, 8), (4, 40, 10), (1, 48, 14))]
+    specs2 = [dict(ndim=2, dims=(24, 16), n_samples=3, n_chains=2, temps=geometric_temps(0.3, 1.5, 16), sim_seed=8),
+              dict(ndim=2, dims=(24, 16), n_samples=2, n_chains=1, temps=geometric_temps(0.3, 1.5, 9), sim_seed=8,
+                   sample_offset=3)]
+    batched = [gpu_of(**kw) for kw in specs + specs2]
+    b = Batch(batched, mcs_per_launch=3)
+    b.run(2)
+    for kw, sim in zip(specs + specs2, batched):
+        orc = oracle_of(oracle_mod, **_okw(kw))
+        orc.mcs(6)
+        assert_same_state(sim, orc, f"batched T={len(kw['temps'])} C={kw['n_chains']}")
+    b.close()
