@@ -57,8 +57,9 @@ typedef enum {
   SG_ENOMEM = 2,        /* the caller's device buffer is smaller than sg_query_bytes()   */
   SG_ECUDA = 3,         /* a CUDA call failed; the handle is poisoned                    */
   SG_ETIMEOUT = 4,      /* a bounded device-side wait expired; the handle is poisoned    */
-  SG_EUNSUPPORTED = 5   /* valid but outside what this engine implements (odd extents,
+  SG_EUNSUPPORTED = 5,  /* valid but outside what this engine implements (odd extents,
                            a lattice too large for the resident kernels, ...)          */
+  SG_ELIMIT = 6         /* the job exceeds a fixed capacity of the call (see the call)   */
 } sg_status;
 
 enum { SG_PACKED32 = 0, SG_INT8 = 1 };
@@ -182,6 +183,24 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
                           uintptr_t stream, sg_batch **out);
 sg_status sg_batch_run(sg_batch *b, int32_t n_launches, uintptr_t stream);
 void sg_batch_destroy(sg_batch *b);
+
+/* n_sweeps Metropolis sweeps by the streaming (global-memory) path, allocating nothing
+ * and using no scratch from the handle's buffer.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory -- a host framework that owns all
+ * device memory and hands a job only its state, or code that runs while a CUDA graph is
+ * being captured, where cudaMalloc is not allowed -- and still want a sweep whose
+ * working memory is not theirs to provide.
+ * Results are bit-identical to sg_sweep on the same handle.
+ * Working memory: one file-scope device array in the library (about 8.9 MB, holding up
+ * to 4096 (sample, word) pairs: lane-pair tables and bond sums), which every GPU that
+ * loads the library keeps until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  Every call uses the same array and clears what
+ * must start at zero, so calls whose work overlaps on the GPU (other streams, other
+ * threads, other handles) race and must be serialised by the caller.
+ * Errors: SG_ELIMIT if n_samples x words per site exceeds 4096 (words per site =
+ * n_chains x ceil(n_temps / 32)); SG_EUNSUPPORTED for int8 spins. */
+sg_status sg_sweep_streaming_static(sg_handle *h, int32_t n_sweeps, uintptr_t stream);
 
 /* Free the host-side handle.  The caller frees the device buffer afterwards. */
 void sg_destroy(sg_handle *h);

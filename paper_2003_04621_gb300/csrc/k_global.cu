@@ -10,7 +10,39 @@
 #include "sgmc_internal.cuh"
 #include "sgmc_sweep.cuh"
 
+#include <mutex>
+
 namespace sgmc {
+
+// Scratch of the allocation-free streaming sweep (sg_sweep_streaming_static): the
+// lane-pair tables, then the per-replica bond sums, of at most STATIC_SWEEP_ITEMS
+// (sample, word) pairs.  A file-scope device array: every GPU that loads the library
+// holds it until the process exits, and every call shares it.
+static __device__ __align__(256) unsigned char g_sweep_scratch[STATIC_SWEEP_BYTES];
+
+namespace {
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[64] = {nullptr};
+} // namespace
+
+// Device address of g_sweep_scratch on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress, once per device with that device current, and cached.
+cudaError_t static_sweep_scratch(void **ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sweep_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *ptr = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
 
 __global__ void k_pair_tables(Job jb, Dev dv, uint2 *tables) {
   // one warp per (sample, word): the table of the word's 32 lanes

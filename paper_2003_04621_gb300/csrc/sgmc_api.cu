@@ -758,6 +758,27 @@ sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t 
   return SG_OK;
 }
 
+sg_status sg_sweep_streaming_static(sg_handle *h, int32_t n_sweeps, uintptr_t stream) {
+  if (!h || n_sweeps < 0) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->int8fmt) return SG_EUNSUPPORTED;
+  if ((long long)h->job.S * h->job.W > STATIC_SWEEP_ITEMS) return SG_ELIMIT;
+  if (n_sweeps == 0) return SG_OK;
+  void *base = nullptr;
+  sg_status r = check(h, static_sweep_scratch(&base)); // first call on a device: symbol lookup
+  if (r != SG_OK) return r;
+  uint2 *tables = reinterpret_cast<uint2 *>(base);
+  uint32_t *esum = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + STATIC_SWEEP_TABLES);
+  cudaStream_t st = as_stream(stream);
+  // the array keeps the previous call's contents: the bond sums must start at zero
+  r = check(h, cudaMemsetAsync(esum, 0, (size_t)h->job.S * h->job.W * 32 * 4, st));
+  for (int a = 0; a < n_sweeps && r == SG_OK; ++a) {
+    r = check(h, launch_global_sweep(h->job, h->dev, tables, esum, st));
+    if (r == SG_OK) h->t_metro += 1;
+  }
+  return r;
+}
+
 void sg_destroy(sg_handle *h) { delete h; }
 
 const char *sg_strerror(sg_status s) {
@@ -768,6 +789,7 @@ const char *sg_strerror(sg_status s) {
   case SG_ECUDA: return "CUDA error";
   case SG_ETIMEOUT: return "bounded device wait expired";
   case SG_EUNSUPPORTED: return "unsupported parameters";
+  case SG_ELIMIT: return "exceeds a fixed capacity of the call";
   }
   return "unknown status";
 }

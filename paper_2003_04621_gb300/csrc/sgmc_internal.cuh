@@ -333,6 +333,12 @@ cudaError_t launch_exchange_batch(JobDesc *jobs, int n_jobs, cudaStream_t st);
 cudaError_t prepare_resident_kernels(int max_smem);
 cudaError_t prepare_houdayer_kernels(int max_smem);
 cudaError_t launch_global_sweep(const Job &jb, const Dev &dv, uint2 *tables, uint32_t *esum, cudaStream_t st);
+// Capacity of the allocation-free streaming sweep's static scratch: (sample, word) pairs,
+// each a 2 KB lane-pair table and 128 bytes of bond sums (about 8.9 MB in all).
+constexpr int STATIC_SWEEP_ITEMS = 4096;
+constexpr size_t STATIC_SWEEP_TABLES = (size_t)STATIC_SWEEP_ITEMS * 256 * 8;
+constexpr size_t STATIC_SWEEP_BYTES = STATIC_SWEEP_TABLES + (size_t)STATIC_SWEEP_ITEMS * 32 * 4;
+cudaError_t static_sweep_scratch(void **ptr);
 cudaError_t launch_global_energy(const Job &jb, const Dev &dv, uint2 *tables, uint32_t *esum, cudaStream_t st);
 int houdayer_smem(const Job &jb, int bitmaps_smem);
 size_t houdayer_scratch_bytes(const Job &jb);

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libsgmc.so")
 SG_PACKED32 = 0
 SG_INT8 = 1
 
-STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETIMEOUT", 5: "SG_EUNSUPPORTED"}
+STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETIMEOUT", 5: "SG_EUNSUPPORTED",
+          6: "SG_ELIMIT"}
 
 
 class SGError(RuntimeError):
@@ -51,7 +52,7 @@ EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_run_mcs", "sg_measure",
     "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
-    "sg_batch_run", "sg_batch_destroy", "sg_destroy", "sg_strerror",
+    "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
 
 _lib = None
@@ -88,6 +89,7 @@ def lib():
         "sg_get_launch": [P, P, P, P],
         "sg_batch_create": [P, I32, I32, U, ctypes.POINTER(P)],
         "sg_batch_run": [P, I32, U],
+        "sg_sweep_streaming_static": [P, I32, U],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -210,6 +212,10 @@ class Simulation:
 
     def run_mcs(self, n: int = 1, stream=None):
         _check(lib().sg_run_mcs(self._h, int(n), self._s(stream)), "sg_run_mcs")
+
+    def sweep_streaming_static(self, n: int = 1, stream=None):
+        """Sweeps that allocate nothing (library-held scratch; see sgmc.h)."""
+        _check(lib().sg_sweep_streaming_static(self._h, int(n), self._s(stream)), "sg_sweep_streaming_static")
 
     # -- observables and state --------------------------------------------------------
     def measure(self, stream=None):
