@@ -104,7 +104,8 @@ def dist_env():
 
 def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int):
     """Time the CPU oracle, as it is, on `n_samples` samples of the workload for `n_mcs`
-    MCS each, one oracle per thread (ctypes releases the GIL)."""
+    MCS each (with the workload's Houdayer moves), one oracle per thread (ctypes
+    releases the GIL)."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
@@ -117,7 +118,7 @@ def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int):
         o = oracle.Oracle(oracle.OracleParams(workload.ndim, workload.dims, S, workload.n_chains,
                                               list(workload.temps), coupling_seed=workload.coupling_seed,
                                               sim_seed=workload.sim_seed, sample_offset=off))
-        o.mcs(n_mcs)
+        o.mcs(n_mcs, houdayer=bool(workload.houdayer))
         return S
 
     t0 = time.perf_counter()
@@ -252,6 +253,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--shape", default=None, help="fixed resident launch shape THREADSxWORDS (no autotuning)")
+    ap.add_argument("--workload", default="3d_l16", choices=["3d_l16", "2d_l128_houdayer"],
+                    help="3d_l16: the headline job; 2d_l128_houdayer: Metropolis + Houdayer + exchange")
     ap.add_argument("--serve-jobs", type=int, default=20)
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -273,10 +277,14 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
-    w = workload_3d_l16().with_(sample_offset=rank * 1024)
+    from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer
+
+    base = workload_3d_l16() if args.workload == "3d_l16" else workload_2d_l128_houdayer()
+    w = base.with_(sample_offset=rank * base.n_samples)
     stream = torch.cuda.Stream()
     kw = dict(ndim=w.ndim, dims=w.dims, n_samples=w.n_samples, n_chains=w.n_chains, temps=list(w.temps),
-              coupling_seed=w.coupling_seed, sim_seed=w.sim_seed, sample_offset=w.sample_offset)
+              coupling_seed=w.coupling_seed, sim_seed=w.sim_seed, sample_offset=w.sample_offset,
+              houdayer=w.houdayer)
     sim = Simulation(stream=stream, **kw)
     attempts_per_step = w.attempts_per_sweep
 
@@ -287,7 +295,11 @@ def main():
     # pick the resident kernel's launch shape on a scratch copy (results do not depend on it)
     from paper_2003_04621_gb300 import autotune
 
-    tuning = autotune.tune(sim, stream=stream)
+    if args.shape:
+        nt, words = (int(x) for x in args.shape.lower().split("x"))
+        sim.set_launch(nt, words)
+    else:
+        autotune.tune(sim, stream=stream)
     launch = sim.launch()
     for _ in range(max(args.warmup, 3)):
         sim.run_mcs(1)
@@ -359,21 +371,28 @@ def main():
             traffic = json.load(open(prof)).get("resident_packed_3d_l16_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
+    houd = args.workload == "2d_l128_houdayer"
+    launches_per_step = 3 if houd else 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic (seeded +-J couplings and hot start)",
-        "config": {"workload": w.name, "lattice": "3D L=16 periodic", "samples_per_gpu": w.n_samples,
-                   "chains": w.n_chains, "temps": w.T, "temp_range": [0.9, 2.0], "spin_format": "packed32",
-                   "step": "one MCS = checkerboard Metropolis sweep + replica exchange, one fused launch",
+        "config": {"workload": w.name,
+                   "lattice": "2D L=128 periodic" if houd else "3D L=16 periodic", "samples_per_gpu": w.n_samples,
+                   "chains": w.n_chains, "temps": w.T,
+                   "temp_range": [round(w.temps[0], 6), round(w.temps[-1], 6)], "spin_format": "packed32",
+                   "step": ("one MCS = Metropolis sweep, one Houdayer move per (sample, temperature) pair, "
+                            "exchange: 3 launches") if houd else
+                           "one MCS = checkerboard Metropolis sweep + replica exchange, one fused launch",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"samples x{ws}",
                    "launch": launch},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "wall_s": wall,
         "clocks": clk,
         "roofline": {"bound": "alu", "achieved": achieved_tips, "peak": peak_tips, "unit": "Tinstr/s",
-                     "frac": achieved_tips / peak_tips, "traffic": traffic,
-                     "kernel": f"k_resident_packed<3,{launch['threads']},{launch['words']},fused PT>",
+                     "frac": achieved_tips / peak_tips, "traffic": traffic if not houd else None,
+                     "kernel": f"k_resident_packed<{w.ndim},{launch['threads']},{launch['words']},fused exchange>"
+                     if not houd else "whole MCS (3 kernels; see profiles/)",
                      "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled)",
                      "instr_per_attempt": instr_per_attempt},
         "hbm_effective": {"achieved_gbs": hbm_eff, "peak_gbs": pk["hbm_gbs"], "frac": hbm_eff / pk["hbm_gbs"],
@@ -385,10 +404,11 @@ def main():
         line["serving"] = bench_serving(args.serve_jobs)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        v, dt, done = cpu_baseline(w, cores, 40, cores)
+        mcs = 8 if houd else 120  # about 20 s of oracle work on 16 cores
+        v, dt, done = cpu_baseline(w, cores, mcs, cores)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{done} of the {w.n_samples} samples x 40 MCS, one oracle thread per "
-                                          f"sample ({dt:.1f} s wall)"}
+                                "sample": f"{done} of the {w.n_samples} samples x {mcs} MCS, one oracle thread per "
+                                          f"sample ({dt:.1f} s wall, {dt * cores:.0f} core-s)"}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
