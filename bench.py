@@ -95,13 +95,6 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int):
     """Time the CPU oracle, as it is, on `n_samples` samples of the workload for `n_mcs`
     MCS each (with the workload's Houdayer moves), one oracle per thread (ctypes
@@ -131,21 +124,33 @@ def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int):
 
 def run_reference(args, ws, rank):
     """Reference arm: the CPU oracle on the host cores, same metric and workload."""
-    from paper_2003_04621_gb300.inputs import workload_3d_l16
+    from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer, workload_3d_l16
 
     if rank != 0:
         return
-    w = workload_3d_l16()
+    w = workload_3d_l16() if args.workload == "3d_l16" else workload_2d_l128_houdayer()
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    oracle.build()
     cores = os.cpu_count() or 1
     samples_per_step = cores
-    for _ in range(args.warmup):
-        cpu_baseline(w, cores, 1, samples_per_step)
-    t0 = time.perf_counter()
-    total_attempts = 0
-    for _ in range(args.steps):
-        _, _, done = cpu_baseline(w, cores, 1, samples_per_step)
-        total_attempts += w.N * w.n_chains * w.T * done
-    dt = time.perf_counter() - t0
+    # one oracle per host thread, each holding one sample of the job (created untimed)
+    orcs = [oracle.Oracle(oracle.OracleParams(w.ndim, w.dims, 1, w.n_chains, list(w.temps),
+                                              coupling_seed=w.coupling_seed, sim_seed=w.sim_seed, sample_offset=s))
+            for s in range(samples_per_step)]
+    houd = bool(w.houdayer)
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        def step():
+            list(ex.map(lambda o: o.mcs(1, houdayer=houd), orcs))
+
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        dt = time.perf_counter() - t0
+    total_attempts = w.N * w.n_chains * w.T * samples_per_step * args.steps
     value = total_attempts / (dt * 1e9)
     sample = f"{samples_per_step} of the {w.n_samples} samples x 1 MCS per step, one oracle thread per sample"
     print(json.dumps({
@@ -153,8 +158,9 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded couplings and hot start)",
-        "config": {"workload": w.name, "lattice": "3D L=16 periodic", "samples": w.n_samples, "chains": 2,
-                   "temps": 32, "parallelism": "cpu threads over samples"},
+        "config": {"workload": w.name, "lattice": f"{w.ndim}D L={w.dims[0]} periodic", "samples": w.n_samples,
+                   "chains": w.n_chains, "temps": w.T, "houdayer": bool(w.houdayer),
+                   "parallelism": "cpu threads over samples"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -258,6 +264,8 @@ def main():
                     help="3d_l16: the headline job; 2d_l128_houdayer: Metropolis + Houdayer + exchange")
     ap.add_argument("--serve-jobs", type=int, default=20)
     args = ap.parse_args()
+    from paper_2003_04621_gb300.shard import dist_env, max_over_ranks, weak_shard
+
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
@@ -280,7 +288,7 @@ def main():
     from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer
 
     base = workload_3d_l16() if args.workload == "3d_l16" else workload_2d_l128_houdayer()
-    w = base.with_(sample_offset=rank * base.n_samples)
+    w = weak_shard(base, rank)
     stream = torch.cuda.Stream()
     kw = dict(ndim=w.ndim, dims=w.dims, n_samples=w.n_samples, n_chains=w.n_chains, temps=list(w.temps),
               coupling_seed=w.coupling_seed, sim_seed=w.sim_seed, sample_offset=w.sample_offset,
@@ -326,10 +334,7 @@ def main():
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, device="cuda")
     value = attempts_per_step * ws * args.steps / (total_ms * 1e6)
     mean_launch_ms = total_ms / args.steps
 
