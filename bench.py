@@ -168,10 +168,11 @@ def run_reference(args, ws, rank):
 
 def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1):
     """The uneven 3D batch (153 jobs of L = 8..32 and 16..48 temperatures) advanced
-    `mcs_per_launch` MCS per CUDA-graph launch: the jobs of one lattice size are swept by
-    one resident launch (a job table in the kernel's parameters), the five sizes run as
-    parallel branches.  Compared with the uniform L=16 job advanced the same number of MCS
-    per launch."""
+    `mcs_per_launch` MCS per CUDA-graph launch: the jobs of one lattice size and words per
+    chain are swept by one resident launch (a job table in the kernel's parameters), the
+    groups run as parallel branches.  Compared with (a) the same jobs advanced one after
+    another through the plain per-job path (identical results), and (b) the uniform
+    L=16 x 32-temperature job, all advanced the same number of MCS per launch."""
     import torch
 
     from paper_2003_04621_gb300 import autotune
@@ -192,33 +193,39 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
         return a.elapsed_time(e)
 
     jobs = workload_batched_uneven()
-    # the largest job of each lattice size leads its group: tune its shape, order it first
-    by_L = {}
+    # one launch shape per (lattice size, words per chain) group, tuned on a stand-in with
+    # the group's samples and 32 or 48 temperatures; the group's largest job leads it
+    groups = {}
     for w in jobs:
-        by_L.setdefault(w.dims[0], []).append(w)
+        groups.setdefault((w.dims[0], (w.T + 31) // 32), []).append(w)
     ordered, shapes = [], {}
-    for L, ws in by_L.items():
+    for key, ws in groups.items():
         ws.sort(key=lambda w: -w.n_samples * w.T)
         ordered.extend(ws)
     sims = [mk(w) for w in ordered]
     k = 0
-    for L, ws in by_L.items():
-        # tune the lattice size on a stand-in with the size's total samples and 32 temps
-        rep = Simulation(3, (L, L, L), sum(w.n_samples for w in ws), 2, geometric_temps(0.9, 2.0, 32), stream=stream)
+    for (L, wc), ws in groups.items():
+        rep = Simulation(3, (L, L, L), sum(w.n_samples for w in ws), 2, geometric_temps(0.9, 2.0, 32 * wc - 16 * (wc - 1)),
+                         stream=stream)
         autotune.tune(rep, stream=stream)
-        shapes[L] = rep.launch()
+        shapes[(L, wc)] = rep.launch()
         rep.close()
         for s_ in sims[k:k + len(ws)]:
-            s_.set_launch(shapes[L]["threads"], shapes[L]["words"])
+            s_.set_launch(shapes[(L, wc)]["threads"], shapes[(L, wc)]["words"])
         k += len(ws)
+    attempts_per_mcs = sum(w.attempts_per_sweep for w in jobs)
+    # (a) the plain path: every job alone, one after another
+    for s_ in sims:
+        s_.run_mcs(mcs_per_launch, stream=stream)
+    pms = timed(lambda n: [s_.run_mcs(mcs_per_launch, stream=stream) for _ in range(n) for s_ in sims], 1)
+    plain = attempts_per_mcs * mcs_per_launch / (pms * 1e6)
     b = Batch(sims, mcs_per_launch=mcs_per_launch, stream=stream)
     b.run(warmup, stream=stream)
     ms = timed(lambda n: b.run(n, stream=stream), steps)
-    attempts = sum(w.attempts_per_sweep for w in jobs) * steps * mcs_per_launch
     b.close()
     for s_ in sims:
         s_.close()
-    # the uniform single-size plain path, the same MCS per launch
+    # (b) the uniform single-size job
     u = workload_3d_l16()
     us = mk(u)
     autotune.tune(us, stream=stream)
@@ -226,12 +233,18 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
     ums = timed(lambda n: [us.run_mcs(mcs_per_launch, stream=stream) for _ in range(n)], steps)
     uni = u.attempts_per_sweep * steps * mcs_per_launch / (ums * 1e6)
     us.close()
-    value = attempts / (ms * 1e6)
+    value = attempts_per_mcs * steps * mcs_per_launch / (ms * 1e6)
+    # fraction of the 32-replica words' lanes that hold a replica (the rest are masked)
+    lanes = sum(w.N * w.n_samples * w.n_chains * 32 * ((w.T + 31) // 32) for w in jobs)
     return {"workload": "3D L in {8,12,16,24,32} x {2048,1024,512,128,32} samples, 16..48 temps per sample",
             "jobs": len(jobs), "value": value, "unit": UNIT, "launches": steps, "mcs_per_launch": mcs_per_launch,
-            "ms_per_mcs": ms / (steps * mcs_per_launch), "uniform_plain_value": uni, "vs_uniform_plain": value / uni,
-            "shapes": {str(L): v for L, v in shapes.items()},
-            "launch": "per graph launch: one resident launch per lattice size (job table), sizes in parallel"}
+            "ms_per_mcs": ms / (steps * mcs_per_launch),
+            "plain_same_jobs_value": plain, "vs_plain_same_jobs": value / plain,
+            "uniform_l16_value": uni, "vs_uniform_l16": value / uni,
+            "lane_occupancy": attempts_per_mcs / lanes,
+            "shapes": {f"L{L}_wc{wc}": v for (L, wc), v in shapes.items()},
+            "launch": "per graph launch: one resident launch per (L, words per chain) group (job table), "
+                      "groups in parallel"}
 
 
 def bench_serving(n_jobs: int, rate: float = 50.0):
@@ -339,16 +352,18 @@ def main():
     mean_launch_ms = total_ms / args.steps
 
     # end to end through the public API: create from host parameters, then per step one
-    # MCS and a device->host read of the observables (E by slot and N q)
+    # MCS and a device->host read of the observables (E by slot and N q) into pinned memory
     e2e = None
     if rank == 0 or ws > 1:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim2 = Simulation(stream=stream, **kw)
         sim2.set_launch(launch["threads"], launch["words"])
+        E = torch.empty((w.n_samples, w.n_chains, w.T), dtype=torch.int32, pin_memory=True).numpy()
+        Q = torch.empty((w.n_samples, w.T), dtype=torch.int32, pin_memory=True).numpy()
         for _ in range(args.steps):
             sim2.run_mcs(1, stream=stream)
-            E, Q = sim2.measure(stream=stream)
+            sim2.measure(stream=stream, out=(E, Q))
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         d2h = E.nbytes + Q.nbytes
@@ -377,7 +392,8 @@ def main():
         except (OSError, ValueError):
             traffic = None
     houd = args.workload == "2d_l128_houdayer"
-    launches_per_step = 3 if houd else 1
+    # Houdayer MCS: sweep, q maps, cluster labels, flips, energies with the exchange
+    launches_per_step = 5 if houd else 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -387,7 +403,7 @@ def main():
                    "chains": w.n_chains, "temps": w.T,
                    "temp_range": [round(w.temps[0], 6), round(w.temps[-1], 6)], "spin_format": "packed32",
                    "step": ("one MCS = Metropolis sweep, one Houdayer move per (sample, temperature) pair, "
-                            "exchange: 3 launches") if houd else
+                            "exchange: 5 launches") if houd else
                            "one MCS = checkerboard Metropolis sweep + replica exchange, one fused launch",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"samples x{ws}",
                    "launch": launch},
@@ -397,7 +413,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_tips, "peak": peak_tips, "unit": "Tinstr/s",
                      "frac": achieved_tips / peak_tips, "traffic": traffic if not houd else None,
                      "kernel": f"k_resident_packed<{w.ndim},{launch['threads']},{launch['words']},fused exchange>"
-                     if not houd else "whole MCS (3 kernels; see profiles/)",
+                     if not houd else "whole MCS (5 kernels; see profiles/)",
                      "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled)",
                      "instr_per_attempt": instr_per_attempt},
         "hbm_effective": {"achieved_gbs": hbm_eff, "peak_gbs": pk["hbm_gbs"], "frac": hbm_eff / pk["hbm_gbs"],

@@ -135,16 +135,219 @@ __device__ __forceinline__ void close_row(const uint32_t (&Q)[RW], const uint32_
   }
 }
 
+// Canonical site of bitmap block b, lane l (row r = b / RW, x = 32 (b % RW) + l) as a
+// colour-split index p; `valid` is false for the padding bits past L0.
+__device__ __forceinline__ int block_site(const Geo &g, int RW, int b, int l, bool &valid) {
+  const int r = b / RW, x = 32 * (b - r * RW) + l;
+  valid = x < g.L0;
+  const int y = r % g.L1, z = r / g.L1;
+  const int c = (x + y + z) & 1;
+  return c * g.Nh + r * g.H + (x >> 1);
+}
+
+// Phase 0: the two chains' slot maps of sample s and the byte tables of the lane
+// permutations: sig maps chain-1 lane b -> chain-0 lane a = perm0[slot1[b]] (built when
+// `sig` is given), sigi maps chain-0 lane a -> chain-1 lane b = perm1[slot0[a]] (when
+// `sigi` is given).  Ends with a CTA barrier.
+__device__ __forceinline__ void houd_tables(const Job &jb, const Dev &dv, int s, int32_t *perm0, int32_t *perm1,
+                                            int32_t *slot0, int32_t *slot1, uint32_t *sig, uint32_t *sigi) {
+  const int T = jb.T, tid = threadIdx.x;
+  if (tid < 32) {
+    const size_t c0 = ((size_t)s * jb.C + 0) * T, c1 = ((size_t)s * jb.C + 1) * T;
+    perm0[tid] = tid < T ? dv.perm[c0 + tid] : 0;
+    perm1[tid] = tid < T ? dv.perm[c1 + tid] : 0;
+    slot0[tid] = tid < T ? dv.slot[c0 + tid] : 0;
+    slot1[tid] = tid < T ? dv.slot[c1 + tid] : 0;
+  }
+  __syncthreads();
+  for (int e = tid; e < 1024; e += blockDim.x) {
+    const int j = e >> 8, v = e & 255;
+    uint32_t o1 = 0u, o2 = 0u;
+#pragma unroll
+    for (int bb = 0; bb < 8; ++bb) {
+      const int lanei = 8 * j + bb;
+      if (((v >> bb) & 1) && lanei < T) {
+        o1 |= 1u << perm0[slot1[lanei]];
+        o2 |= 1u << perm1[slot0[lanei]];
+      }
+    }
+    if (sig) sig[e] = o1;
+    if (sigi) sigi[e] = o2;
+  }
+  __syncthreads();
+}
+
+// Phase 1: the q bitmap of every pair of sample s (pair a's bitmap at Qb + a * NBW) and
+// its number M of q = -1 sites, added into Mc[a].  Warps stride over the 32-site blocks.
+__device__ __forceinline__ void houd_qmaps(const Job &jb, int RW, const uint32_t *w0p, const uint32_t *w1p,
+                                           const uint32_t *sig, uint32_t *Qb, int NBW, uint32_t *Mc) {
+  const int T = jb.T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t tmask = T >= 32 ? FULLM : ((1u << T) - 1u);
+  uint32_t mpart = 0u;
+  for (int b = warp; b < NBW; b += nwarps) {
+    bool valid;
+    const int p = block_site(jb.g, RW, b, lane, valid);
+    uint32_t qa = 0u;
+    if (valid) qa = (w0p[p] ^ permute_word(sig, w1p[p])) & tmask;
+    const uint32_t col = transpose32(qa, lane); // lane a: bit l = q of pair a at site l
+    if (lane < T) {
+      Qb[(size_t)lane * NBW + b] = col;
+      mpart += __popc(col);
+    }
+  }
+  if (lane < T && mpart) atomicAdd(&Mc[lane], mpart);
+}
+
+// Phase 2 for one pair, by one warp: choose the seed (the floor(u M / 2^32)-th q = -1 site
+// in canonical order) and grow its q = -1 cluster into C (zeroed here) over rows.  The
+// worklist (stack of rows, in-list bits, size) is the warp's own.  Returns the cluster's
+// size on every lane (0 when M = 0).
+template <int D, int RW>
+__device__ uint32_t houd_fill_pair(const Geo &g, const uint32_t *Q, uint32_t *C, int NBW, uint32_t M, uint32_t u,
+                                   uint16_t *stack, uint32_t *inlist, int *ssize, unsigned long long *err) {
+  const int lane = threadIdx.x & 31;
+  const int L0 = g.L0, L1 = g.L1, R = g.R;
+  for (int b = lane; b < NBW; b += 32) C[b] = 0u;
+  __syncwarp();
+  if (M == 0u) return 0u;
+  const uint32_t n = (uint32_t)(((unsigned long long)u * M) >> 32);
+  // the n-th set bit in canonical order: contiguous chunks per lane, then a warp scan
+  const int chunk = (NBW + 31) / 32;
+  const int b0 = lane * chunk, b1 = min(NBW, b0 + chunk);
+  uint32_t cnt = 0u;
+  for (int b = b0; b < b1; ++b) cnt += __popc(Q[b]);
+  uint32_t pre = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(FULLM, pre, o);
+    if (lane >= o) pre += v;
+  }
+  pre -= cnt; // exclusive
+  int seed_b = -1, seed_bit = 0;
+  if (n >= pre && n < pre + cnt) {
+    uint32_t rem = n - pre;
+    for (int b = b0; b < b1; ++b) {
+      uint32_t w = Q[b];
+      const uint32_t pc = __popc(w);
+      if (rem < pc) {
+        for (uint32_t i = 0; i < rem; ++i) w &= w - 1u; // drop the lowest `rem` set bits
+        seed_b = b;
+        seed_bit = __ffs(w) - 1;
+        break;
+      }
+      rem -= pc;
+    }
+  }
+  const unsigned owner = __ballot_sync(FULLM, seed_b >= 0);
+  const int src = __ffs(owner) - 1;
+  seed_b = __shfl_sync(FULLM, seed_b, src);
+  seed_bit = __shfl_sync(FULLM, seed_bit, src);
+  for (int i = lane; i < (R + 31) / 32; i += 32) inlist[i] = 0u;
+  __syncwarp();
+  if (lane == 0) {
+    const int r0 = seed_b / RW;
+    uint32_t q[RW], x[RW], f[RW];
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      q[m] = Q[r0 * RW + m];
+      x[m] = (r0 * RW + m == seed_b) ? (1u << seed_bit) : 0u;
+    }
+    close_row<RW>(q, x, f, L0);
+#pragma unroll
+    for (int m = 0; m < RW; ++m) C[r0 * RW + m] = f[m];
+    stack[0] = (uint16_t)r0;
+    inlist[r0 >> 5] |= 1u << (r0 & 31);
+    *ssize = 1;
+  }
+  __syncwarp();
+  // rows: each round pops up to 32 queued rows, one per lane
+  const int max_rounds = 4 * g.N + 64; // never reached: every push adds at least one site
+  for (int round = 0; round < max_rounds; ++round) {
+    const int size = *ssize;
+    if (size == 0) break;
+    const int take = min(32, size);
+    int r = -1;
+    if (lane < take) {
+      r = stack[size - 1 - lane];
+      atomicAnd(&inlist[r >> 5], ~(1u << (r & 31)));
+    }
+    __syncwarp();
+    if (lane == 0) *ssize = size - take;
+    __syncwarp();
+    if (r >= 0) {
+      const int y = r % L1, z = r / L1;
+      int nrow[2 * (D - 1)];
+      nrow[0] = (y + 1 == L1) ? r - (L1 - 1) : r + 1;
+      nrow[1] = (y == 0) ? r + (L1 - 1) : r - 1;
+      if (D == 3) {
+        const int L2 = g.L2;
+        nrow[2] = (z + 1 == L2) ? r - (L2 - 1) * L1 : r + L1;
+        nrow[3] = (z == 0) ? r + (L2 - 1) * L1 : r - L1;
+      }
+#pragma unroll
+      for (int t = 0; t < 2 * (D - 1); ++t) {
+        const int nr = nrow[t];
+        uint32_t q[RW], x[RW], f[RW];
+        bool any = false;
+#pragma unroll
+        for (int m = 0; m < RW; ++m) {
+          q[m] = Q[nr * RW + m];
+          x[m] = q[m] & C[r * RW + m] & ~C[nr * RW + m];
+          any |= x[m] != 0u;
+        }
+        if (!any) continue;
+        close_row<RW>(q, x, f, L0);
+        bool changed = false;
+#pragma unroll
+        for (int m = 0; m < RW; ++m) {
+          const uint32_t old = atomicOr(&C[nr * RW + m], f[m]);
+          changed |= (f[m] & ~old) != 0u;
+        }
+        if (changed) {
+          const uint32_t bit = 1u << (nr & 31);
+          if (!(atomicOr(&inlist[nr >> 5], bit) & bit)) {
+            const int pos = atomicAdd(ssize, 1);
+            stack[pos] = (uint16_t)nr;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && *ssize > 0) atomicOr(err, ERR_HOUD_ROUNDS);
+  uint32_t sz = 0u;
+  for (int b = lane; b < NBW; b += 32) sz += __popc(C[b]);
+  return __reduce_add_sync(FULLM, sz);
+}
+
+// Phase 3: flip both replicas of every pair of sample s on its cluster (pair a's
+// cluster bitmap at Cb + a * NBW; pairs whose bit in `skip` is set have no cluster).
+__device__ __forceinline__ void houd_flips(const Job &jb, int RW, const uint32_t *Cb, int NBW, uint32_t skip,
+                                           const uint32_t *sigi, uint32_t *w0w, uint32_t *w1w) {
+  const int T = jb.T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool mine = lane < T && !((skip >> lane) & 1u);
+  for (int b = warp; b < NBW; b += nwarps) {
+    const uint32_t cw = mine ? Cb[(size_t)lane * NBW + b] : 0u;
+    if (!__any_sync(FULLM, cw != 0u)) continue;
+    const uint32_t f0 = transpose32(cw, lane); // lane l: bit a = site l in pair a's cluster
+    bool valid;
+    const int p = block_site(jb.g, RW, b, lane, valid);
+    if (valid && f0) {
+      w0w[p] ^= f0;
+      w1w[p] ^= permute_word(sigi, f0);
+    }
+  }
+}
+
 } // namespace
 
 struct HoudArgs {
-  int RW;           // words per bitmap row
-  int NBW;          // words per bitmap (rows x RW)
-  int bitmaps_smem; // 1: q and cluster bitmaps in shared memory, 0: in `scratch`
-  uint32_t *scratch; // [S][2][T][NBW] when not in shared memory
+  int RW;  // words per bitmap row
+  int NBW; // words per bitmap (rows x RW)
 };
 
-// Shared-memory map of the Houdayer kernel.
+// Shared-memory map of the single-CTA Houdayer kernel (bitmaps_smem = 0 leaves out the
+// bitmaps, for sizing only).
 __host__ __device__ inline int houd_smem_bytes(int T, int R, int NBW, int bitmaps_smem, int *off_q, int *off_wl) {
   int off = 0;
   off += 2 * 1024 * 4;      // sig, sigi tables
@@ -158,14 +361,18 @@ __host__ __device__ inline int houd_smem_bytes(int T, int R, int NBW, int bitmap
   return (off + 15) & ~15;
 }
 
+__host__ __device__ inline int houd_worklist_bytes(int R) { return ((2 * R + 3) & ~3) + 4 * ((R + 31) / 32) + 4; }
+
+// Single-CTA form: one CTA of 1024 threads per sample runs all three phases, the
+// bitmaps in shared memory.
 template <int D, int RW>
 __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geo g = jb.g;
-  const int T = jb.T, N = g.N, L0 = g.L0, L1 = g.L1, R = g.R;
+  const int T = jb.T, N = g.N, R = g.R;
   const int NBW = ha.NBW;
   int off_q, off_wl;
-  houd_smem_bytes(T, R, NBW, ha.bitmaps_smem, &off_q, &off_wl);
+  houd_smem_bytes(T, R, NBW, 1, &off_q, &off_wl);
   uint32_t *sig = reinterpret_cast<uint32_t *>(smem);
   uint32_t *sigi = sig + 1024;
   int32_t *perm0 = reinterpret_cast<int32_t *>(sigi + 1024);
@@ -177,225 +384,465 @@ __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
   const uint32_t t_houd = (uint32_t)dv.ctr[CTR_THOUD];
   const int s = blockIdx.x;
   const uint32_t s_glob = (uint32_t)(jb.s_off + s);
-  uint32_t *Qb, *Cb;
-  if (ha.bitmaps_smem) {
-    Qb = reinterpret_cast<uint32_t *>(smem + off_q);
-  } else {
-    Qb = ha.scratch + (size_t)s * 2 * T * NBW;
-  }
-  Cb = Qb + (size_t)T * NBW;
-  unsigned char *wlbase = smem + off_wl;
-  const int wl_bytes = ((2 * R + 3) & ~3) + 4 * ((R + 31) / 32) + 4;
-  uint16_t *stack = reinterpret_cast<uint16_t *>(wlbase + warp * wl_bytes);
-  uint32_t *inlist = reinterpret_cast<uint32_t *>(wlbase + warp * wl_bytes + ((2 * R + 3) & ~3));
+  uint32_t *Qb = reinterpret_cast<uint32_t *>(smem + off_q);
+  uint32_t *Cb = Qb + (size_t)T * NBW;
+  const int wl_bytes = houd_worklist_bytes(R);
+  unsigned char *wl = smem + off_wl + warp * wl_bytes;
+  uint16_t *stack = reinterpret_cast<uint16_t *>(wl);
+  uint32_t *inlist = reinterpret_cast<uint32_t *>(wl + ((2 * R + 3) & ~3));
   int *ssize = reinterpret_cast<int *>(inlist + (R + 31) / 32);
 
-  const uint32_t *w0p = dv.spins + ((size_t)s * jb.W + 0) * N; // chain 0 word (Wc = 1)
-  const uint32_t *w1p = dv.spins + ((size_t)s * jb.W + 1) * N; // chain 1 word
-  uint32_t *w0w = const_cast<uint32_t *>(w0p), *w1w = const_cast<uint32_t *>(w1p);
+  uint32_t *w0w = dv.spins + ((size_t)s * jb.W + 0) * N; // chain 0 word (Wc = 1)
+  uint32_t *w1w = dv.spins + ((size_t)s * jb.W + 1) * N; // chain 1 word
 
-  // ---- phase 0: maps and lane-permutation tables --------------------------------
-  if (tid < 32) {
-    const size_t c0 = ((size_t)s * jb.C + 0) * T, c1 = ((size_t)s * jb.C + 1) * T;
-    perm0[tid] = tid < T ? dv.perm[c0 + tid] : 0;
-    perm1[tid] = tid < T ? dv.perm[c1 + tid] : 0;
-    slot0[tid] = tid < T ? dv.slot[c0 + tid] : 0;
-    slot1[tid] = tid < T ? dv.slot[c1 + tid] : 0;
-    Mc[tid] = 0u;
-    if (tid < 2) cnts[tid] = 0ull;
-  }
+  if (tid < 32) Mc[tid] = 0u;
+  if (tid < 2) cnts[tid] = 0ull;
+  houd_tables(jb, dv, s, perm0, perm1, slot0, slot1, sig, sigi);
+  houd_qmaps(jb, RW, w0w, w1w, sig, Qb, NBW, Mc);
   __syncthreads();
-  {
-    // entry e = (byte j, value v): sig maps chain-1 lane b -> chain-0 lane a = perm0[slot1[b]],
-    // sigi maps chain-0 lane a -> chain-1 lane b = perm1[slot0[a]]
-    const int j = tid >> 8, v = tid & 255;
-    uint32_t o1 = 0u, o2 = 0u;
-#pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
-      const int lanei = 8 * j + bb;
-      if (((v >> bb) & 1) && lanei < T) {
-        o1 |= 1u << perm0[slot1[lanei]];
-        o2 |= 1u << perm1[slot0[lanei]];
-      }
-    }
-    sig[tid] = o1;
-    sigi[tid] = o2;
-  }
-  __syncthreads();
-
-  const uint32_t tmask = T >= 32 ? FULLM : ((1u << T) - 1u);
-  // canonical site of bitmap block b, lane l: row r = b / RW, x = 32 (b % RW) + l
-  auto site_word = [&](int b, int l, int &p, bool &valid) {
-    const int r = b / RW, x = 32 * (b - r * RW) + l;
-    valid = x < L0;
-    const int y = r % L1, z = r / L1;
-    const int c = (x + y + z) & 1;
-    p = c * g.Nh + r * g.H + (x >> 1);
-  };
-
-  // ---- phase 1: q bitmaps and M ----------------------------------------------------
-  {
-    uint32_t mpart = 0u;
-    for (int b = warp; b < NBW; b += HNT / 32) {
-      int p;
-      bool valid;
-      site_word(b, lane, p, valid);
-      uint32_t qa = 0u;
-      if (valid) qa = (w0p[p] ^ permute_word(sig, w1p[p])) & tmask;
-      const uint32_t col = transpose32(qa, lane); // lane a: bit l = q of pair a at site l
-      if (lane < T) {
-        Qb[(size_t)lane * NBW + b] = col;
-        mpart += __popc(col);
-      }
-    }
-    if (lane < T && mpart) atomicAdd(&Mc[lane], mpart);
-  }
-  __syncthreads();
-
-  // ---- phase 2: one cluster per pair -------------------------------------------------
   for (int a = warp; a < T; a += HNT / 32) {
-    uint32_t *Q = Qb + (size_t)a * NBW;
-    uint32_t *C = Cb + (size_t)a * NBW;
-    for (int b = lane; b < NBW; b += 32) C[b] = 0u;
     const uint32_t M = Mc[a];
-    if (M == 0u) continue;
-    const int k = slot0[a];
-    const uint32_t u = philox10((uint32_t)k, t_houd, s_glob, TAG_HOUD, jb.sk0, jb.sk1).x;
-    const uint32_t n = (uint32_t)(((unsigned long long)u * M) >> 32);
-    // the n-th set bit in canonical order: contiguous chunks per lane, then a warp scan
-    const int chunk = (NBW + 31) / 32;
-    const int b0 = lane * chunk, b1 = min(NBW, b0 + chunk);
-    uint32_t cnt = 0u;
-    for (int b = b0; b < b1; ++b) cnt += __popc(Q[b]);
-    uint32_t pre = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(FULLM, pre, o);
-      if (lane >= o) pre += v;
-    }
-    pre -= cnt; // exclusive
-    int seed_b = -1, seed_bit = 0;
-    if (n >= pre && n < pre + cnt) {
-      uint32_t rem = n - pre;
-      for (int b = b0; b < b1; ++b) {
-        uint32_t w = Q[b];
-        const uint32_t pc = __popc(w);
-        if (rem < pc) {
-          for (uint32_t i = 0; i < rem; ++i) w &= w - 1u; // drop the lowest `rem` set bits
-          seed_b = b;
-          seed_bit = __ffs(w) - 1;
-          break;
-        }
-        rem -= pc;
-      }
-    }
-    const unsigned owner = __ballot_sync(FULLM, seed_b >= 0);
-    const int src = __ffs(owner) - 1;
-    seed_b = __shfl_sync(FULLM, seed_b, src);
-    seed_bit = __shfl_sync(FULLM, seed_bit, src);
-    // worklist reset
-    for (int i = lane; i < (R + 31) / 32; i += 32) inlist[i] = 0u;
-    __syncwarp();
-    if (lane == 0) {
-      const int r0 = seed_b / RW;
-      uint32_t q[RW], x[RW], f[RW];
-#pragma unroll
-      for (int m = 0; m < RW; ++m) {
-        q[m] = Q[r0 * RW + m];
-        x[m] = (r0 * RW + m == seed_b) ? (1u << seed_bit) : 0u;
-      }
-      close_row<RW>(q, x, f, L0);
-#pragma unroll
-      for (int m = 0; m < RW; ++m) C[r0 * RW + m] = f[m];
-      stack[0] = (uint16_t)r0;
-      inlist[r0 >> 5] |= 1u << (r0 & 31);
-      *ssize = 1;
-    }
-    __syncwarp();
-    // rows: each round pops up to 32 queued rows, one per lane
-    const int max_rounds = 4 * N + 64; // never reached: every push adds at least one site
-    for (int round = 0; round < max_rounds; ++round) {
-      const int size = *ssize;
-      if (size == 0) break;
-      const int take = min(32, size);
-      int r = -1;
-      if (lane < take) {
-        r = stack[size - 1 - lane];
-        atomicAnd(&inlist[r >> 5], ~(1u << (r & 31)));
-      }
-      __syncwarp();
-      if (lane == 0) *ssize = size - take;
-      __syncwarp();
-      if (r >= 0) {
-        const int y = r % L1, z = r / L1;
-        int nrow[2 * (D - 1)];
-        nrow[0] = (y + 1 == L1) ? r - (L1 - 1) : r + 1;
-        nrow[1] = (y == 0) ? r + (L1 - 1) : r - 1;
-        if (D == 3) {
-          const int L2 = g.L2;
-          nrow[2] = (z + 1 == L2) ? r - (L2 - 1) * L1 : r + L1;
-          nrow[3] = (z == 0) ? r + (L2 - 1) * L1 : r - L1;
-        }
-#pragma unroll
-        for (int t = 0; t < 2 * (D - 1); ++t) {
-          const int nr = nrow[t];
-          uint32_t q[RW], x[RW], f[RW];
-          bool any = false;
-#pragma unroll
-          for (int m = 0; m < RW; ++m) {
-            q[m] = Q[nr * RW + m];
-            x[m] = q[m] & C[r * RW + m] & ~C[nr * RW + m];
-            any |= x[m] != 0u;
-          }
-          if (!any) continue;
-          close_row<RW>(q, x, f, L0);
-          bool changed = false;
-#pragma unroll
-          for (int m = 0; m < RW; ++m) {
-            const uint32_t old = atomicOr(&C[nr * RW + m], f[m]);
-            changed |= (f[m] & ~old) != 0u;
-          }
-          if (changed) {
-            const uint32_t bit = 1u << (nr & 31);
-            if (!(atomicOr(&inlist[nr >> 5], bit) & bit)) {
-              const int pos = atomicAdd(ssize, 1);
-              stack[pos] = (uint16_t)nr;
-            }
-          }
-        }
-      }
-      __syncwarp();
-    }
-    if (lane == 0 && *ssize > 0) atomicOr(&dv.ctr[CTR_ERROR], ERR_HOUD_ROUNDS);
-    uint32_t sz = 0u;
-    for (int b = lane; b < NBW; b += 32) sz += __popc(C[b]);
-    sz = __reduce_add_sync(FULLM, sz);
-    if (lane == 0) {
+    const uint32_t u = M ? philox10((uint32_t)slot0[a], t_houd, s_glob, TAG_HOUD, jb.sk0, jb.sk1).x : 0u;
+    const uint32_t sz = houd_fill_pair<D, RW>(g, Qb + (size_t)a * NBW, Cb + (size_t)a * NBW, NBW, M, u, stack,
+                                              inlist, ssize, &dv.ctr[CTR_ERROR]);
+    if (lane == 0 && M) {
       atomicAdd(&cnts[0], 1ull);
       atomicAdd(&cnts[1], (unsigned long long)sz);
     }
   }
   __syncthreads();
-
-  // ---- phase 3: flip both replicas of every pair on its cluster ------------------------
-  for (int b = warp; b < NBW; b += HNT / 32) {
-    const uint32_t cw = lane < T ? Cb[(size_t)lane * NBW + b] : 0u;
-    if (!__any_sync(FULLM, cw != 0u)) continue;
-    const uint32_t f0 = transpose32(cw, lane); // lane l: bit a = site l in pair a's cluster
-    int p;
-    bool valid;
-    site_word(b, lane, p, valid);
-    if (valid && f0) {
-      w0w[p] ^= f0;
-      w1w[p] ^= permute_word(sigi, f0);
-    }
-  }
+  houd_flips(jb, RW, Cb, NBW, 0u, sigi, w0w, w1w);
   __syncthreads();
   if (tid == 0) {
     if (cnts[0]) atomicAdd(&dv.ctr[CTR_HMOVES], cnts[0]);
     if (cnts[1]) atomicAdd(&dv.ctr[CTR_HSITES], cnts[1]);
   }
   grid_done_advance(dv.ctr, 0ull, 0ull, 1ull);
+}
+
+// ---------------------------------------------------------------------------------
+// Split form, used when the handle holds bitmap scratch for every pair.  The single-CTA
+// form runs a sample's pairs in one CTA, so the sample's largest cluster holds the whole
+// CTA, and samples run in waves of one CTA per SM.  Here the q bitmaps are written to
+// scratch by one CTA per sample, then every pair's cluster is grown by its own warp in
+// CTAs of a few pairs, all pairs of all samples in flight together, and the flips are
+// applied by one CTA per sample.
+// ---------------------------------------------------------------------------------
+struct HoudSplit {
+  int RW;        // words per bitmap row
+  int NBW;       // words per bitmap
+  uint32_t *Qg;  // [S][T][NBW] q bitmaps
+  uint32_t *Cg;  // [S][T][NBW] cluster bitmaps
+  uint32_t *Mg;  // [S][32] q = -1 sites per pair (by chain-0 lane)
+  int wpb;       // pairs (warps) per CTA of the fill kernel
+  int in_smem;   // 1: a fill warp copies its bitmaps into shared memory
+};
+constexpr int HSPLIT_NT = 512;     // threads of the per-sample kernels
+constexpr int HFILL_MAX_WARPS = 8; // pairs per CTA of the fill kernel, at most
+constexpr int HFILL_HEAD = 16;     // fill kernel's shared-memory header (two counters)
+
+// The per-sample kernels move the bitmaps between registers and global scratch through a
+// shared-memory tile of HQ_TB blocks for every pair (row stride HQ_TB + 1: the lanes of a
+// warp, one pair each, fall in distinct banks), so the global accesses are contiguous runs
+// of each pair's bitmap.
+constexpr int HQ_TB = 64, HQ_U = 4;
+
+__global__ void __launch_bounds__(HSPLIT_NT) k_houd_q(Job jb, Dev dv, HoudSplit hs) {
+  __shared__ uint32_t sig[1024];
+  __shared__ int32_t maps[4][32];
+  __shared__ uint32_t Mc[32];
+  __shared__ uint32_t stage[32][HQ_TB + 1];
+  const int s = blockIdx.x, T = jb.T, NBW = hs.NBW, RW = hs.RW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = HSPLIT_NT / 32;
+  if (tid < 32) Mc[tid] = 0u;
+  houd_tables(jb, dv, s, maps[0], maps[1], maps[2], maps[3], sig, nullptr);
+  const uint32_t *w0p = dv.spins + ((size_t)s * jb.W + 0) * jb.g.N;
+  const uint32_t *w1p = dv.spins + ((size_t)s * jb.W + 1) * jb.g.N;
+  uint32_t *Qb = hs.Qg + (size_t)s * T * NBW;
+  const uint32_t tmask = T >= 32 ? FULLM : ((1u << T) - 1u);
+  uint32_t mpart = 0u;
+  for (int tb = 0; tb < NBW; tb += HQ_TB) {
+    const int nb = min(HQ_TB, NBW - tb);
+    // HQ_U blocks per warp at a time: their words are loaded before any is used
+    for (int j0 = warp; j0 < nb; j0 += nwarps * HQ_U) {
+      uint32_t x0[HQ_U], x1[HQ_U];
+#pragma unroll
+      for (int u = 0; u < HQ_U; ++u) {
+        const int j = j0 + u * nwarps;
+        x0[u] = x1[u] = 0u;
+        if (j < nb) {
+          bool valid;
+          const int p = block_site(jb.g, RW, tb + j, lane, valid);
+          if (valid) {
+            x0[u] = w0p[p];
+            x1[u] = w1p[p];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < HQ_U; ++u) {
+        const int j = j0 + u * nwarps;
+        if (j < nb) {
+          const uint32_t qa = (x0[u] ^ permute_word(sig, x1[u])) & tmask;
+          const uint32_t col = transpose32(qa, lane); // lane a: bit l = q of pair a at site l
+          stage[lane][j] = col;
+          mpart += lane < T ? __popc(col) : 0u;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < T * nb; e += HSPLIT_NT) {
+      const int a = e / nb, j = e - a * nb;
+      Qb[(size_t)a * NBW + tb + j] = stage[a][j];
+    }
+    __syncthreads();
+  }
+  if (lane < T && mpart) atomicAdd(&Mc[lane], mpart);
+  __syncthreads();
+  if (tid < 32) hs.Mg[(size_t)s * 32 + tid] = Mc[tid];
+}
+
+template <int D, int RW, bool SMEM>
+__global__ void __launch_bounds__(HFILL_MAX_WARPS * 32, 4) k_houd_fill(Job jb, Dev dv, HoudSplit hs) {
+  // dynamic shared memory only (its size attribute is the device's whole opt-in amount):
+  // the CTA's two counters, then one region per warp (bitmaps if in_smem, worklist)
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long *cnts = reinterpret_cast<unsigned long long *>(smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int NBW = hs.NBW, R = jb.g.R;
+  const long long gp = (long long)blockIdx.x * hs.wpb + warp; // pair: sample gp / T, chain-0 lane gp % T
+  const bool active = gp < (long long)jb.S * jb.T;
+  const int s = active ? (int)(gp / jb.T) : 0;
+  const int a = active ? (int)(gp - (long long)s * jb.T) : 0;
+  if (threadIdx.x < 2) cnts[threadIdx.x] = 0ull;
+  const int wl_bytes = houd_worklist_bytes(R);
+  const int per_warp = (SMEM ? 2 * NBW * 4 : 0) + wl_bytes;
+  unsigned char *mine = smem + HFILL_HEAD + (size_t)warp * per_warp;
+  uint32_t *Qs = reinterpret_cast<uint32_t *>(mine);
+  uint32_t *Cs = Qs + NBW;
+  unsigned char *wl = mine + (SMEM ? 2 * NBW * 4 : 0);
+  uint16_t *stack = reinterpret_cast<uint16_t *>(wl);
+  uint32_t *inlist = reinterpret_cast<uint32_t *>(wl + ((2 * R + 3) & ~3));
+  int *ssize = reinterpret_cast<int *>(inlist + (R + 31) / 32);
+  __syncthreads();
+  if (active) {
+    const uint32_t M = hs.Mg[(size_t)s * 32 + a];
+    uint32_t *Qp = hs.Qg + ((size_t)s * jb.T + a) * NBW;
+    uint32_t *Cp = hs.Cg + ((size_t)s * jb.T + a) * NBW;
+    if (M) {
+      const uint32_t t_houd = (uint32_t)dv.ctr[CTR_THOUD];
+      const int k = dv.slot[((size_t)s * jb.C + 0) * jb.T + a];
+      const uint32_t u = philox10((uint32_t)k, t_houd, (uint32_t)(jb.s_off + s), TAG_HOUD, jb.sk0, jb.sk1).x;
+      const uint32_t *Q = Qp;
+      uint32_t *C = Cp;
+      if (SMEM) {
+        for (int b = lane; b < NBW; b += 32) Qs[b] = Qp[b];
+        __syncwarp();
+        Q = Qs;
+        C = Cs;
+      }
+      const uint32_t sz = houd_fill_pair<D, RW>(jb.g, Q, C, NBW, M, u, stack, inlist, ssize, &dv.ctr[CTR_ERROR]);
+      if (SMEM) {
+        __syncwarp();
+        for (int b = lane; b < NBW; b += 32) Cp[b] = Cs[b];
+      }
+      if (lane == 0) {
+        atomicAdd(&cnts[0], 1ull);
+        atomicAdd(&cnts[1], (unsigned long long)sz);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (cnts[0]) atomicAdd(&dv.ctr[CTR_HMOVES], cnts[0]);
+    if (cnts[1]) atomicAdd(&dv.ctr[CTR_HSITES], cnts[1]);
+  }
+}
+
+__global__ void __launch_bounds__(HSPLIT_NT) k_houd_flip(Job jb, Dev dv, HoudSplit hs) {
+  __shared__ uint32_t sigi[1024];
+  __shared__ int32_t maps[4][32];
+  __shared__ uint32_t stage[32][HQ_TB + 1];
+  __shared__ uint32_t skip_s;
+  const int s = blockIdx.x, T = jb.T, NBW = hs.NBW, RW = hs.RW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = HSPLIT_NT / 32;
+  houd_tables(jb, dv, s, maps[0], maps[1], maps[2], maps[3], nullptr, sigi);
+  // pairs without a q = -1 site have no cluster (their bitmaps were not written)
+  if (warp == 0) {
+    const uint32_t skip = __ballot_sync(FULLM, lane >= T || hs.Mg[(size_t)s * 32 + lane] == 0u);
+    if (lane == 0) skip_s = skip;
+  }
+  __syncthreads();
+  const uint32_t skip = skip_s;
+  uint32_t *w0w = dv.spins + ((size_t)s * jb.W + 0) * jb.g.N;
+  uint32_t *w1w = dv.spins + ((size_t)s * jb.W + 1) * jb.g.N;
+  const uint32_t *Cb = hs.Cg + (size_t)s * T * NBW;
+  for (int tb = 0; tb < NBW; tb += HQ_TB) {
+    const int nb = min(HQ_TB, NBW - tb);
+    for (int e = tid; e < T * nb; e += HSPLIT_NT) {
+      const int a = e / nb, j = e - a * nb;
+      stage[a][j] = ((skip >> a) & 1u) ? 0u : Cb[(size_t)a * NBW + tb + j];
+    }
+    __syncthreads();
+    for (int j0 = warp; j0 < nb; j0 += nwarps * HQ_U) {
+      uint32_t f[HQ_U], x0[HQ_U], x1[HQ_U];
+      int pp[HQ_U];
+#pragma unroll
+      for (int u = 0; u < HQ_U; ++u) {
+        const int j = j0 + u * nwarps;
+        f[u] = 0u;
+        pp[u] = -1;
+        if (j < nb) {
+          const uint32_t cw = lane < T ? stage[lane][j] : 0u;
+          if (__any_sync(FULLM, cw != 0u)) {
+            f[u] = transpose32(cw, lane); // lane l: bit a = site l in pair a's cluster
+            bool valid;
+            const int p = block_site(jb.g, RW, tb + j, lane, valid);
+            if (valid && f[u]) pp[u] = p;
+          }
+        }
+        x0[u] = pp[u] >= 0 ? w0w[pp[u]] : 0u;
+        x1[u] = pp[u] >= 0 ? w1w[pp[u]] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < HQ_U; ++u) {
+        if (pp[u] >= 0) {
+          w0w[pp[u]] = x0[u] ^ f[u];
+          w1w[pp[u]] = x1[u] ^ permute_word(sigi, f[u]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  grid_done_advance(dv.ctr, 0ull, 0ull, 1ull);
+}
+
+// ---------------------------------------------------------------------------------
+// Labelling form of phase 2: one CTA per pair labels every q = -1 cluster of the pair by
+// union-find over the runs of its bitmap rows, then keeps the cluster of the seed.
+//
+// A run is a maximal row segment of q = -1 sites, cut at x = 0 (so no run wraps); runs
+// are numbered in canonical order, and the run of site (row r, x) is the number of run
+// starts at or before it minus one.  Unions: the runs at x = 0 and x = L0-1 of a row
+// (periodic wrap), and for every pair of neighbouring rows (y+1, and z+1 in 3D) the two
+// runs over each segment where both rows have q = -1.  The forest links the larger root
+// under the smaller with a compare-and-swap, so parents only ever decrease and every
+// walk up a tree ends; finds halve the path they walk.  The work is proportional to the
+// runs, and the CTA's threads share it, so no pair waits on a long serial fill.
+// ---------------------------------------------------------------------------------
+constexpr int HLAB_NT = 256;
+
+__device__ __forceinline__ int uf_find(volatile int32_t *par, int x) {
+  for (;;) {
+    const int p = par[x];
+    if (p == x) return x;
+    const int q = par[p];
+    if (q == p) return p;
+    par[x] = q; // path halving: q is an ancestor of x
+    x = q;
+  }
+}
+
+__device__ __forceinline__ void uf_union(volatile int32_t *par, int a, int b) {
+  for (;;) {
+    a = uf_find(par, a);
+    b = uf_find(par, b);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicCAS(const_cast<int32_t *>(par) + b, b, a);
+    if (old == b) return;
+    b = old; // b was linked meanwhile: continue from its new parent (smaller than b)
+  }
+}
+
+// Position of the j-th (from 0) set bit of w; w has more than j set bits.
+__device__ __forceinline__ int nth_set_bit(uint32_t w, int j) {
+  for (int q = 0; q < j; ++q) w &= w - 1u;
+  return __ffs(w) - 1;
+}
+
+// Run number of site (row r, x) from the run-start bitmap and the per-word start counts.
+template <int RW>
+__device__ __forceinline__ int run_of(const uint32_t *St, const int32_t *pre, int r, int x) {
+  const int i = r * RW + (x >> 5), b = x & 31;
+  return pre[i] + __popc(St[i] & (0xFFFFFFFFu >> (31 - b))) - 1;
+}
+
+// Exclusive prefix sum over the CTA of one value per thread (HLAB_NT threads); the total
+// goes to *total.  `ws` holds HLAB_NT / 32 ints.  Contains CTA barriers.
+__device__ __forceinline__ int cta_exclusive_scan(int v, int *ws, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULLM, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = lane < HLAB_NT / 32 ? ws[lane] : 0;
+    int iw = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULLM, iw, o);
+      if (lane >= o) iw += t;
+    }
+    if (lane < HLAB_NT / 32) ws[lane] = iw - w;
+    if (lane == HLAB_NT / 32 - 1) ws[HLAB_NT / 32] = iw;
+  }
+  __syncthreads();
+  const int ex = ws[warp] + inc - v;
+  *total = ws[HLAB_NT / 32];
+  __syncthreads();
+  return ex;
+}
+
+// Shared-memory bytes of the labelling kernel: Q, run starts, run counts per word, parents
+// (at most N/2 runs), scan space, neighbour rows.
+__host__ __device__ inline int label_smem_bytes(int NBW, int N, int R, int D) {
+  return 4 * (3 * NBW + N / 2 + 32) + ((2 * (D - 1) * R + 7) & ~7);
+}
+
+template <int D, int RW>
+__global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSplit hs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Geo g = jb.g;
+  const int NBW = hs.NBW, L0 = g.L0, L1 = g.L1, R = g.R;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int s = (int)(blockIdx.x / (unsigned)jb.T), a = (int)(blockIdx.x - (unsigned)s * jb.T);
+  const uint32_t M = hs.Mg[(size_t)s * 32 + a];
+  if (M == 0u) return; // no q = -1 site: no move (the flip kernel skips the pair)
+  uint32_t *Q = reinterpret_cast<uint32_t *>(smem);
+  uint32_t *St = Q + NBW;
+  int32_t *pre = reinterpret_cast<int32_t *>(St + NBW); // runs before each word
+  int32_t *par = pre + NBW;
+  int32_t *misc = par + g.N / 2; // [0..8] scan space, [16] seed root, [17] size
+  uint16_t *nrow = reinterpret_cast<uint16_t *>(misc + 32); // [D-1][R] next row along y (and z)
+  const uint32_t *Qp = hs.Qg + ((size_t)s * jb.T + a) * NBW;
+  uint32_t *Cp = hs.Cg + ((size_t)s * jb.T + a) * NBW;
+  for (int i = tid; i < NBW; i += HLAB_NT) Q[i] = Qp[i];
+  for (int r = tid; r < R; r += HLAB_NT) {
+    const int y = r % L1, z = r / L1;
+    nrow[r] = (uint16_t)((y + 1 == L1) ? r - (L1 - 1) : r + 1);
+    if (D == 3) nrow[R + r] = (uint16_t)((z + 1 == g.L2) ? r - (g.L2 - 1) * L1 : r + L1);
+  }
+  if (tid == 0) misc[17] = 0;
+  __syncthreads();
+
+  // run starts (runs cut at x = 0), counted per word (contiguous chunks of words per thread)
+  const int chunk = (NBW + HLAB_NT - 1) / HLAB_NT;
+  const int i0 = min(NBW, tid * chunk), i1 = min(NBW, i0 + chunk);
+  int nst = 0;
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t w = Q[i];
+    const uint32_t prev = (i % RW) ? (Q[i - 1] >> 31) : 0u;
+    const uint32_t st = w & ~((w << 1) | prev);
+    St[i] = st;
+    nst += __popc(st);
+    pre[i] = nst; // inclusive, within the chunk (made global below)
+  }
+  int nruns;
+  const int run0 = cta_exclusive_scan(nst, misc, &nruns);
+  for (int i = i0; i < i1; ++i) pre[i] = run0 + pre[i] - __popc(St[i]); // runs before word i
+  __syncthreads();
+  for (int i = tid; i < nruns; i += HLAB_NT) par[i] = i;
+  __syncthreads();
+
+  // unions: the row's wrap (at the row's first word), and the two runs over each overlap
+  // segment with the next rows along y (and z), segments cut at the word edge
+  volatile int32_t *vpar = par;
+  for (int i = tid; i < NBW; i += HLAB_NT) {
+    const int r = i / RW, m = i - r * RW;
+    const uint32_t w = Q[i];
+    if (m == 0 && (w & 1u) && ((Q[r * RW + ((L0 - 1) >> 5)] >> ((L0 - 1) & 31)) & 1u))
+      uf_union(vpar, run_of<RW>(St, pre, r, 0), run_of<RW>(St, pre, r, L0 - 1));
+#pragma unroll
+    for (int t = 0; t < D - 1; ++t) {
+      const int r2 = nrow[t * R + r];
+      const uint32_t o = w & Q[r2 * RW + m];
+      uint32_t seg = o & ~(o << 1);
+      while (seg) {
+        const int x = 32 * m + __ffs(seg) - 1;
+        seg &= seg - 1u;
+        uf_union(vpar, run_of<RW>(St, pre, r, x), run_of<RW>(St, pre, r2, x));
+      }
+    }
+  }
+  __syncthreads();
+  // parents := roots.  The walks only read, and each run's entry is written by its own
+  // thread with its root, so a walk through it meets either value and ends at that root.
+  for (int i = tid; i < nruns; i += HLAB_NT) {
+    int x = i;
+    for (int p = vpar[x]; p != x; p = vpar[x]) x = p;
+    vpar[i] = x;
+  }
+  __syncthreads();
+
+  // the seed: the floor(u M / 2^32)-th q = -1 site in canonical order (warp 0)
+  if (warp == 0) {
+    const uint32_t t_houd = (uint32_t)dv.ctr[CTR_THOUD];
+    const int k = dv.slot[((size_t)s * jb.C + 0) * jb.T + a];
+    const uint32_t uu = philox10((uint32_t)k, t_houd, (uint32_t)(jb.s_off + s), TAG_HOUD, jb.sk0, jb.sk1).x;
+    const uint32_t n = (uint32_t)(((unsigned long long)uu * M) >> 32);
+    const int ch = (NBW + 31) / 32;
+    const int b0 = min(NBW, lane * ch), b1 = min(NBW, b0 + ch);
+    uint32_t c = 0u;
+    for (int b = b0; b < b1; ++b) c += __popc(Q[b]);
+    uint32_t pre_c = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(FULLM, pre_c, o);
+      if (lane >= o) pre_c += v;
+    }
+    pre_c -= c;
+    if (n >= pre_c && n < pre_c + c) {
+      uint32_t rem = n - pre_c;
+      for (int b = b0; b < b1; ++b) {
+        const uint32_t w = Q[b];
+        const uint32_t pc = __popc(w);
+        if (rem < pc) {
+          const int r = b / RW, x = 32 * (b - r * RW) + nth_set_bit(w, (int)rem);
+          misc[16] = par[run_of<RW>(St, pre, r, x)];
+          break;
+        }
+        rem -= pc;
+      }
+    }
+  }
+  __syncthreads();
+
+  // the seed's cluster: the runs whose root is the seed's root
+  const int root0 = misc[16];
+  uint32_t size = 0u;
+  for (int i = tid; i < NBW; i += HLAB_NT) {
+    const uint32_t w = Q[i];
+    uint32_t seg = w & ~(w << 1), c = 0u;
+    if (seg) {
+      const int r = i / RW, x0 = 32 * (i - r * RW);
+      // the run of the word's first segment; every later segment starts the next run
+      int id = run_of<RW>(St, pre, r, x0 + __ffs(seg) - 1) - 1;
+      while (seg) {
+        const int b = __ffs(seg) - 1;
+        seg &= seg - 1u;
+        ++id;
+        if (par[id] == root0) c |= ((w + (1u << b)) ^ w) & w;
+      }
+    }
+    Cp[i] = c;
+    size += __popc(c);
+  }
+  size = __reduce_add_sync(FULLM, size);
+  if (lane == 0 && size) atomicAdd(&misc[17], (int)size);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&dv.ctr[CTR_HMOVES], 1ull);
+    atomicAdd(&dv.ctr[CTR_HSITES], (unsigned long long)misc[17]);
+  }
 }
 
 int houdayer_smem(const Job &jb, int bitmaps_smem) {
@@ -406,11 +853,13 @@ int houdayer_smem(const Job &jb, int bitmaps_smem) {
 
 size_t houdayer_scratch_bytes(const Job &jb) {
   const int RW = (jb.g.L0 + 31) / 32;
-  return (size_t)jb.S * 2 * jb.T * (size_t)(jb.g.R * RW) * 4;
+  // q and cluster bitmaps of every pair, then M per (sample, lane)
+  return (size_t)jb.S * 2 * jb.T * (size_t)(jb.g.R * RW) * 4 + (size_t)jb.S * 32 * 4;
 }
 
 namespace {
 typedef void (*houd_fn)(Job, Dev, HoudArgs);
+typedef void (*fill_fn)(Job, Dev, HoudSplit);
 template <int D>
 houd_fn pick_houd(int RW) {
   switch (RW) {
@@ -424,30 +873,107 @@ houd_fn pick_houd(int RW) {
   default: return k_houdayer<D, 8>;
   }
 }
+template <int D, bool SMEM>
+fill_fn pick_fill_rw(int RW) {
+  switch (RW) {
+  case 1: return k_houd_fill<D, 1, SMEM>;
+  case 2: return k_houd_fill<D, 2, SMEM>;
+  case 3: return k_houd_fill<D, 3, SMEM>;
+  case 4: return k_houd_fill<D, 4, SMEM>;
+  case 5: return k_houd_fill<D, 5, SMEM>;
+  case 6: return k_houd_fill<D, 6, SMEM>;
+  case 7: return k_houd_fill<D, 7, SMEM>;
+  default: return k_houd_fill<D, 8, SMEM>;
+  }
+}
+template <int D>
+fill_fn pick_label_rw(int RW) {
+  switch (RW) {
+  case 1: return k_houd_label<D, 1>;
+  case 2: return k_houd_label<D, 2>;
+  case 3: return k_houd_label<D, 3>;
+  case 4: return k_houd_label<D, 4>;
+  case 5: return k_houd_label<D, 5>;
+  case 6: return k_houd_label<D, 6>;
+  case 7: return k_houd_label<D, 7>;
+  default: return k_houd_label<D, 8>;
+  }
+}
+fill_fn pick_label(int d, int RW) { return d == 2 ? pick_label_rw<2>(RW) : pick_label_rw<3>(RW); }
+
+fill_fn pick_fill(int d, int RW, bool in_smem) {
+  if (d == 2) return in_smem ? pick_fill_rw<2, true>(RW) : pick_fill_rw<2, false>(RW);
+  return in_smem ? pick_fill_rw<3, true>(RW) : pick_fill_rw<3, false>(RW);
+}
+
+// Fill-kernel shape: up to 8 pairs per CTA, fewer when their bitmaps would take more than
+// 64 KB of shared memory; bitmaps stay in global scratch when even one pair's exceed the
+// Houdayer shared-memory budget.
+void fill_shape(const Job &jb, int NBW, int *wpb, int *in_smem, int *smem) {
+  const int wl = houd_worklist_bytes(jb.g.R);
+  const int per = 2 * NBW * 4 + wl;
+  int w = HFILL_MAX_WARPS;
+  while (w > 1 && w * per > 64 * 1024) w >>= 1;
+  if (w * per <= HOUD_SMEM_BUDGET) {
+    *wpb = w;
+    *in_smem = 1;
+    *smem = HFILL_HEAD + w * per;
+  } else {
+    *wpb = HFILL_MAX_WARPS;
+    *in_smem = 0;
+    *smem = HFILL_HEAD + HFILL_MAX_WARPS * wl;
+  }
+}
 } // namespace
 
 cudaError_t prepare_houdayer_kernels(int max_smem) {
   for (int rw = 1; rw <= 8; ++rw) {
     for (int d = 2; d <= 3; ++d) {
-      const houd_fn fn = d == 2 ? pick_houd<2>(rw) : pick_houd<3>(rw);
-      const cudaError_t e =
-          cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-      if (e != cudaSuccess) return e;
+      const void *fns[4] = {(const void *)(d == 2 ? pick_houd<2>(rw) : pick_houd<3>(rw)),
+                            (const void *)pick_fill(d, rw, true), (const void *)pick_fill(d, rw, false),
+                            (const void *)pick_label(d, rw)};
+      for (const void *fn : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+      }
     }
   }
   return cudaSuccess;
 }
 
+// With `scratch` (houdayer_scratch_bytes of the handle's buffer) the split form runs;
+// without it the single-CTA form, whose bitmaps must then fit `smem_limit`.
 cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, cudaStream_t st) {
+  const int RW = (jb.g.L0 + 31) / 32;
+  const int NBW = jb.g.R * RW;
+  if (scratch) {
+    HoudSplit hs;
+    hs.RW = RW;
+    hs.NBW = NBW;
+    hs.Qg = scratch;
+    hs.Cg = scratch + (size_t)jb.S * jb.T * NBW;
+    hs.Mg = hs.Cg + (size_t)jb.S * jb.T * NBW;
+    int smem = 0;
+    fill_shape(jb, NBW, &hs.wpb, &hs.in_smem, &smem);
+    const long long pairs = (long long)jb.S * jb.T;
+    k_houd_q<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    const int lab = label_smem_bytes(NBW, jb.g.N, jb.g.R, jb.g.d);
+    if (lab <= HOUD_SMEM_BUDGET) {
+      pick_label(jb.g.d, RW)<<<(unsigned)pairs, HLAB_NT, (size_t)lab, st>>>(jb, dv, hs);
+    } else {
+      // labels beyond the shared-memory budget: grow the seed's cluster row by row
+      pick_fill(jb.g.d, RW, hs.in_smem != 0)<<<(unsigned)((pairs + hs.wpb - 1) / hs.wpb), 32 * hs.wpb,
+                                                (size_t)smem, st>>>(jb, dv, hs);
+    }
+    k_houd_flip<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    return cudaGetLastError();
+  }
   HoudArgs ha;
-  ha.RW = (jb.g.L0 + 31) / 32;
-  ha.NBW = jb.g.R * ha.RW;
-  const int in_smem = houdayer_smem(jb, 1);
-  ha.bitmaps_smem = in_smem <= smem_limit ? 1 : 0;
-  ha.scratch = scratch;
-  if (!ha.bitmaps_smem && !scratch) return cudaErrorInvalidValue;
-  const int smem = houdayer_smem(jb, ha.bitmaps_smem);
-  const houd_fn fn = jb.g.d == 2 ? pick_houd<2>(ha.RW) : pick_houd<3>(ha.RW);
+  ha.RW = RW;
+  ha.NBW = NBW;
+  const int smem = houdayer_smem(jb, 1);
+  if (smem > smem_limit) return cudaErrorInvalidValue;
+  const houd_fn fn = jb.g.d == 2 ? pick_houd<2>(RW) : pick_houd<3>(RW);
   fn<<<(unsigned)jb.S, HNT, (size_t)smem, st>>>(jb, dv, ha);
   return cudaGetLastError();
 }

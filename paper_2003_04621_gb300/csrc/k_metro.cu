@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       if (warp < WPC) {
         int32_t U = 0;
         for (int wq = 0; wq < NT / 32; ++wq) U += epart[warp * NT + wq * 32 + lane];
-        EL(my_ci)[my_j0 + lane] = 2 * U - D * g.N;
+        // held chains (T <= 64) keep their energies for the exchange; otherwise the
+        // energies go straight to global memory (the per-chain slots hold 64 replicas)
+        if (nch > 0) EL(my_ci)[my_j0 + lane] = 2 * U - D * g.N;
+        else if (lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = 2 * U - D * g.N;
       }
       __syncthreads();
     }
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     }
   }
 
-  if (warp < WPC && lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = EL(my_ci)[my_j0 + lane];
+  if (nch > 0 && warp < WPC && lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = EL(my_ci)[my_j0 + lane];
   if (warp < nch) {
     const size_t cb = ((size_t)s * jb.C + c0 + warp) * jb.T;
 #pragma unroll

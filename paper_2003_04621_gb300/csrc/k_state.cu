@@ -168,26 +168,19 @@ __global__ void k_gather_energy(Job jb, Dev dv, int32_t *E_out) {
   E_out[idx] = dv.E[base + dv.perm[idx]];
 }
 
-// N q (Eq. 4) per (sample, slot): CTA per (sample, slot); q = -1 sites are those where
-// the chain-0 and chain-1 replicas at the slot differ.
-__global__ void k_overlap(Job jb, Dev dv, int int8fmt, int32_t *Q_out) {
+// N q (Eq. 4) per (sample, slot), int8 layout: CTA per (sample, slot); q = -1 sites are
+// those where the chain-0 and chain-1 replicas at the slot differ.
+__global__ void k_overlap_int8(Job jb, Dev dv, int32_t *Q_out) {
   const Geo g = jb.g;
   const int s = blockIdx.x / jb.T;
   const int k = blockIdx.x - s * jb.T;
   const int a = dv.perm[((size_t)s * jb.C + 0) * jb.T + k];
   const int b = dv.perm[((size_t)s * jb.C + 1) * jb.T + k];
+  const int8_t *sp = reinterpret_cast<const int8_t *>(dv.spins);
+  const int8_t *pa = sp + ((size_t)s * jb.C + 0) * g.N * jb.Tp + a;
+  const int8_t *pb = sp + ((size_t)s * jb.C + 1) * g.N * jb.Tp + b;
   int cnt = 0;
-  if (int8fmt) {
-    const int8_t *sp = reinterpret_cast<const int8_t *>(dv.spins);
-    const int8_t *pa = sp + ((size_t)s * jb.C + 0) * g.N * jb.Tp + a;
-    const int8_t *pb = sp + ((size_t)s * jb.C + 1) * g.N * jb.Tp + b;
-    for (int p = threadIdx.x; p < g.N; p += blockDim.x) cnt += pa[(size_t)p * jb.Tp] != pb[(size_t)p * jb.Tp];
-  } else {
-    const uint32_t *wa = dv.spins + ((size_t)s * jb.W + 0 * jb.Wc + a / 32) * g.N;
-    const uint32_t *wb = dv.spins + ((size_t)s * jb.W + 1 * jb.Wc + b / 32) * g.N;
-    const int la = a & 31, lb = b & 31;
-    for (int p = threadIdx.x; p < g.N; p += blockDim.x) cnt += ((wa[p] >> la) ^ (wb[p] >> lb)) & 1u;
-  }
+  for (int p = threadIdx.x; p < g.N; p += blockDim.x) cnt += pa[(size_t)p * jb.Tp] != pb[(size_t)p * jb.Tp];
   __shared__ int red[32];
   cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
@@ -196,6 +189,63 @@ __global__ void k_overlap(Job jb, Dev dv, int int8fmt, int32_t *Q_out) {
     int v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0;
     v = __reduce_add_sync(0xFFFFFFFFu, v);
     if (threadIdx.x == 0) Q_out[blockIdx.x] = g.N - 2 * v;
+  }
+}
+
+// N q per (sample, slot), packed layout: CTA per (sample, block of 32 slots).  The CTA
+// stages the sample's W word planes through shared memory in tiles of `tl` sites
+// (16-byte coalesced loads, several in flight per thread); then lane = slot, and each
+// warp counts over its share of the tile's sites the q = -1 sites of the lane's pair,
+// reading the two words it needs from shared memory (one broadcast per word).  N is a
+// multiple of 4 (every extent even), so every word plane starts 16-byte aligned.
+constexpr int OV_NT = 256, OV_TILE = 1024, OV_SMEM = 44 * 1024; // with the static 1 KB, under 48 KB
+
+// Sites per tile: up to OV_TILE, fewer when the W planes would exceed OV_SMEM bytes; a
+// multiple of 4.
+inline int overlap_tile(int W) {
+  int tl = OV_SMEM / (4 * W);
+  tl = tl > OV_TILE ? OV_TILE : tl;
+  return tl & ~3;
+}
+
+__global__ void __launch_bounds__(OV_NT) k_overlap_packed(Job jb, Dev dv, int tl, int32_t *Q_out) {
+  extern __shared__ __align__(16) uint32_t tile[]; // [W][tl]
+  __shared__ uint32_t red[OV_NT / 32][32];
+  const Geo g = jb.g;
+  const int nblk = (jb.T + 31) >> 5;
+  const int s = blockIdx.x / nblk, blk = blockIdx.x - s * nblk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blk * 32 + lane;
+  const bool valid = k < jb.T;
+  const int a = valid ? dv.perm[((size_t)s * jb.C + 0) * jb.T + k] : 0;
+  const int b = valid ? dv.perm[((size_t)s * jb.C + 1) * jb.T + k] : 0;
+  const uint32_t *ta = tile + (size_t)(a >> 5) * tl;
+  const uint32_t *tb = tile + (size_t)(jb.Wc + (b >> 5)) * tl;
+  const int la = a & 31, lb = b & 31;
+  const int W = jb.W;
+  const uint4 *src = reinterpret_cast<const uint4 *>(dv.spins + (size_t)s * W * g.N);
+  const int n4 = g.N >> 2;
+  uint32_t cnt = 0u;
+  for (int base = 0; base < g.N; base += tl) {
+    const int len = min(tl, g.N - base); // a multiple of 4
+    const int len4 = len >> 2;
+    __syncthreads();
+    for (int e = threadIdx.x; e < W * len4; e += OV_NT) {
+      const int w = e / len4, i = e - w * len4;
+      reinterpret_cast<uint4 *>(tile + (size_t)w * tl)[i] = src[(size_t)w * n4 + (base >> 2) + i];
+    }
+    __syncthreads();
+    const int per = (len + OV_NT / 32 - 1) / (OV_NT / 32);
+    const int p0 = warp * per, p1 = min(len, p0 + per);
+    for (int p = p0; p < p1; ++p) cnt += ((ta[p] >> la) ^ (tb[p] >> lb)) & 1u;
+  }
+  red[warp][lane] = cnt;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = 0u;
+#pragma unroll
+    for (int w = 0; w < OV_NT / 32; ++w) v += red[w][lane];
+    if (valid) Q_out[(size_t)s * jb.T + k] = g.N - 2 * (int32_t)v;
   }
 }
 
@@ -244,7 +294,14 @@ cudaError_t launch_import_couplings(const Job &jb, const Dev &dv, const int8_t *
 cudaError_t launch_measure(const Job &jb, const Dev &dv, bool int8fmt, int32_t *E_out, int32_t *Q_out,
                            cudaStream_t st) {
   k_gather_energy<<<blocks_for((long long)jb.S * jb.C * jb.T, 256), 256, 0, st>>>(jb, dv, E_out);
-  if (Q_out && jb.C >= 2) k_overlap<<<(unsigned)(jb.S * jb.T), 256, 0, st>>>(jb, dv, int8fmt ? 1 : 0, Q_out);
+  if (Q_out && jb.C >= 2) {
+    if (int8fmt) k_overlap_int8<<<(unsigned)(jb.S * jb.T), 256, 0, st>>>(jb, dv, Q_out);
+    else {
+      const int tl = overlap_tile(jb.W);
+      k_overlap_packed<<<(unsigned)(jb.S * ((jb.T + 31) / 32)), OV_NT, (size_t)jb.W * tl * 4, st>>>(jb, dv, tl,
+                                                                                                Q_out);
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -135,9 +135,11 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   // streaming sweep path: lane-pair threshold tables and per-replica bond sums
   L.gtab = take(S * (size_t)jb.W * 256 * 8);
   L.esum = take(S * (size_t)jb.W * 32 * 4);
-  // Houdayer bitmaps that do not fit the kernel's shared-memory budget
+  // Houdayer bitmap scratch of the split move: for jobs that make the move every MCS, and
+  // for lattices whose bitmaps exceed the single-CTA kernel's shared-memory budget
   L.houd_bytes = 0;
-  if (houdayer_possible(p, jb) && houdayer_smem(jb, 1) > HOUD_SMEM_BUDGET) L.houd_bytes = houdayer_scratch_bytes(jb);
+  if (houdayer_possible(p, jb) && (p->houdayer || houdayer_smem(jb, 1) > HOUD_SMEM_BUDGET))
+    L.houd_bytes = houdayer_scratch_bytes(jb);
   L.houd = take(L.houd_bytes);
   L.total = off;
   return L;
@@ -262,8 +264,7 @@ sg_status recompute_energy(sg_handle *h, cudaStream_t st) {
 // The cluster move itself (spins only; energies are stale until recomputed).
 sg_status houdayer_move(sg_handle *h, cudaStream_t st) {
   uint32_t *scratch = h->lay.houd_bytes ? reinterpret_cast<uint32_t *>(h->buf + h->lay.houd) : nullptr;
-  const int limit = h->lay.houd_bytes ? 0 : HOUD_SMEM_BUDGET;
-  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, limit, st));
+  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, HOUD_SMEM_BUDGET, st));
   if (r == SG_OK) h->t_houd += 1;
   return r;
 }

@@ -218,10 +218,22 @@ class Simulation:
         _check(lib().sg_sweep_streaming_static(self._h, int(n), self._s(stream)), "sg_sweep_streaming_static")
 
     # -- observables and state --------------------------------------------------------
-    def measure(self, stream=None):
-        """(E by slot [S][C][T], N q [S][T] or None) as numpy arrays; synchronises."""
-        E = np.zeros((self.S, self.C, self.T), np.int32)
-        Q = np.zeros((self.S, self.T), np.int32) if self.C >= 2 else None
+    def measure(self, stream=None, out=None):
+        """(E by slot [S][C][T], N q [S][T] or None) as numpy arrays; synchronises.
+        `out` = (E, Q) writes into given C-contiguous int32 arrays instead (e.g. numpy
+        views of pinned host tensors, so that the device-to-host copies are direct)."""
+        if out is None:
+            E = np.zeros((self.S, self.C, self.T), np.int32)
+            Q = np.zeros((self.S, self.T), np.int32) if self.C >= 2 else None
+        else:
+            E, Q = out
+            if E.dtype != np.int32 or E.shape != (self.S, self.C, self.T) or not E.flags.c_contiguous:
+                raise ValueError("E must be a C-contiguous int32 array of shape [S][C][T]")
+            if self.C >= 2 and (Q is None or Q.dtype != np.int32 or Q.shape != (self.S, self.T)
+                                or not Q.flags.c_contiguous):
+                raise ValueError("Q must be a C-contiguous int32 array of shape [S][T]")
+            if self.C < 2:
+                Q = None
         _check(lib().sg_measure(self._h, E.ctypes.data, Q.ctypes.data if Q is not None else None, self._s(stream)),
                "sg_measure")
         return E, Q

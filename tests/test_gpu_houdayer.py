@@ -49,16 +49,22 @@ def run_pair(oracle_mod, kw, ops, check_every=1):
     return sim, orc
 
 
+# split=False: a handle made without the per-MCS move has no bitmap scratch and runs the
+# single-CTA kernel; split=True: the handle holds the scratch and runs the split form
+# (q maps per sample, one warp per pair, flips per sample).
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("dims", [(16, 16), (40, 24), (66, 4), (2, 8), (8, 2), (96, 6)])
-def test_houdayer_calls_2d(oracle_mod, dims):
+def test_houdayer_calls_2d(oracle_mod, dims, split):
     kw = dict(ndim=2, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.2, 1.6, 8), sim_seed=7,
-              coupling_seed=5)
+              coupling_seed=5, houdayer=split)
     run_pair(oracle_mod, kw, list("sshxshhxsxh"))
 
 
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("dims,T", [((8, 8, 8), 12), ((4, 6, 2), 32), ((16, 4, 8), 5)])
-def test_houdayer_calls_3d(oracle_mod, dims, T):
-    kw = dict(ndim=3, dims=dims, n_samples=2, n_chains=2, temps=geometric_temps(0.5, 2.5, T), sim_seed=19)
+def test_houdayer_calls_3d(oracle_mod, dims, T, split):
+    kw = dict(ndim=3, dims=dims, n_samples=2, n_chains=2, temps=geometric_temps(0.5, 2.5, T), sim_seed=19,
+              houdayer=split)
     run_pair(oracle_mod, kw, list("shxshhx"))
 
 
@@ -80,11 +86,20 @@ def test_houdayer_cold_percolating_clusters(oracle_mod):
 
 
 def test_houdayer_bitmaps_in_global_scratch(oracle_mod):
-    """3D L=32 x 32 temperatures: the pair bitmaps exceed the shared-memory budget and live
-    in the scratch region of the handle's buffer."""
+    """3D L=32 x 32 temperatures: a sample's bitmaps exceed the single-CTA kernel's
+    shared-memory budget, so even a handle made without the per-MCS move holds the
+    scratch and runs the split form."""
     kw = dict(ndim=3, dims=(32, 32, 32), n_samples=1, n_chains=2, temps=geometric_temps(0.9, 2.0, 32),
-              sim_seed=2, houdayer=True)
-    run_pair(oracle_mod, kw, ["m", "m"])
+              sim_seed=2)
+    run_pair(oracle_mod, kw, ["s", "h", "x", "s", "h"])
+
+
+def test_houdayer_fill_in_global_memory(oracle_mod):
+    """2D 256 x 3200: one pair's q and cluster bitmaps (2 x 100 KB) exceed the fill
+    kernel's shared-memory budget, so the clusters are grown in the global scratch."""
+    kw = dict(ndim=2, dims=(256, 3200), n_samples=1, n_chains=2, temps=geometric_temps(0.3, 1.5, 4),
+              sim_seed=4, houdayer=True)
+    run_pair(oracle_mod, kw, ["m", "m", "m"], check_every=3)
 
 
 def test_houdayer_full_size_sampled(oracle_mod):

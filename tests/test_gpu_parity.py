@@ -119,12 +119,13 @@ def test_2d_l128_padded_words(oracle_mod):
         assert_same_state(sim, orc, f"mcs {t}")
 
 
-@pytest.mark.parametrize("fmt", ["packed", "int8"])
-def test_chain_longer_than_a_word(oracle_mod, fmt):
+@pytest.mark.parametrize("fmt,T", [("packed", 40), ("int8", 40), ("packed", 450)])
+def test_chain_longer_than_a_word(oracle_mod, fmt, T):
     """40 temperatures: a chain spans two words, so sweeps and exchange run as separate
-    kernels (the unfused path)."""
-    kw = dict(ndim=3, dims=(4, 6, 4), n_samples=3, n_chains=2, temps=geometric_temps(0.5, 3.0, 40),
-              coupling_seed=9, sim_seed=4, spin_format=fmt)
+    kernels (the unfused path).  450 temperatures: 15 words per chain, so the overlap
+    kernel stages its 30 word planes in tiles shorter than the lattice."""
+    kw = dict(ndim=3, dims=(4, 6, 4) if T < 100 else (8, 8, 8), n_samples=3, n_chains=2,
+              temps=geometric_temps(0.5, 3.0, T), coupling_seed=9, sim_seed=4, spin_format=fmt)
     sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_oracle_kw(kw))
     for t in range(6):
         sim.run_mcs(1)
