@@ -73,6 +73,7 @@ def _load():
         lib.or_sweep.argtypes = [P, ctypes.c_int]
         lib.or_exchange.argtypes = [P]
         lib.or_houdayer.argtypes = [P]
+        lib.or_houdayer_multi.argtypes = [P]
         lib.or_mcs.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         for name in ("or_measure",):
             getattr(lib, name).argtypes = [P, P, P]
@@ -107,6 +108,14 @@ def philox4x32_10(ctr: Sequence[int], key: Sequence[int]) -> tuple[int, int, int
 def _ptr(a: np.ndarray):
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data
+
+
+def _houd_mode(h) -> int:
+    if h is True:
+        return 1
+    if h is False or h is None:
+        return 0
+    return int(h)
 
 
 @dataclass
@@ -166,8 +175,13 @@ class Oracle:
     def houdayer(self):
         self._lib.or_houdayer(self._h)
 
-    def mcs(self, n: int = 1, n_metro: int = 1, houdayer: bool = False):
-        self._lib.or_mcs(self._h, int(n), int(n_metro), int(bool(houdayer)))
+    def houdayer_multi(self):
+        """Multi-cluster variant: every q = -1 cluster of a pair exchanged by its own coin."""
+        self._lib.or_houdayer_multi(self._h)
+
+    def mcs(self, n: int = 1, n_metro: int = 1, houdayer=False):
+        """houdayer: False/0 none, True/1 the single-cluster move, 2 the multi-cluster variant."""
+        self._lib.or_mcs(self._h, int(n), int(n_metro), _houd_mode(houdayer))
 
     # observables and state
     def measure(self):
@@ -243,7 +257,7 @@ class Oracle:
         """Bin means of E and E^2 per temperature slot, measured after every MCS."""
         sE = np.zeros((self.T, n_bins), np.float64)
         sE2 = np.zeros((self.T, n_bins), np.float64)
-        self._lib.or_run_binned(self._h, int(n_mcs), int(n_metro), int(bool(houdayer)), int(bool(pt)),
+        self._lib.or_run_binned(self._h, int(n_mcs), int(n_metro), _houd_mode(houdayer), int(bool(pt)),
                                 int(n_bins), _ptr(sE), _ptr(sE2))
         per = (n_mcs // n_bins) * self.S * self.C
         return sE / per, sE2 / per

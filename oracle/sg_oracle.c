@@ -23,6 +23,7 @@
  *   replica exchange             Sec. 2.2, Eq. 5; temperature<->replica maps as two
  *                                arrays whose entries are swapped (Sec. 3)
  *   Houdayer move                Sec. 2.4, Eq. 10 and the text after it
+ *   multi-cluster variant        Sec. 3 (every cluster exchanged with probability 1/2)
  *   MCS composition              Sec. 2.4 (Metropolis, then Houdayer, then PT)
  *   random numbers               counter-based Philox (Sec. 3, Salmon et al. 2011)
  *   exact enumeration            brute force over all 2^N states (a pin, not a method
@@ -58,6 +59,7 @@
 #define OR_TAG_HOUD 2u
 #define OR_TAG_INIT 3u
 #define OR_TAG_J 4u
+#define OR_TAG_HMULTI 5u
 
 /* ------------------------------------------------------------------------------ */
 /* Philox4x32-10, from Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   */
@@ -463,11 +465,86 @@ void or_houdayer(or_state *st) {
   st->t_houd++;
 }
 
-/* One MCS (Sec. 2.4): n_metro sweeps, one Houdayer move per pair (if on), one PT pass. */
+/* ------------------------------------------------------------------------------ */
+/* Multi-cluster variant of the move (Sec. 3, the remedy for idle threads named    */
+/* there): every q = -1 cluster of a pair is exchanged with probability 1/2, each  */
+/* by its own coin (q = +1 clusters would leave both replicas unchanged).  Reading */
+/* of the coin: the top bit of the Philox word with counter                        */
+/* (i_min, t_houd, s, k << 8 | 5), i_min the cluster's smallest site index.        */
+/* ------------------------------------------------------------------------------ */
+void or_houdayer_multi(or_state *st) {
+  if (st->C < 2) {
+    st->error = 1;
+    return;
+  }
+  const int N = st->N, d = st->ndim;
+  const uint32_t t = st->t_houd;
+  int8_t *q = (int8_t *)malloc((size_t)N);
+  uint8_t *in = (uint8_t *)malloc((size_t)N);
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  for (int s = 0; s < st->S; ++s) {
+    uint32_t sg = (uint32_t)(st->s0 + s);
+    for (int k = 0; k < st->T; ++k) {
+      int a = *at3(st->perm, st, s, 0, k);
+      int b = *at3(st->perm, st, s, 1, k);
+      int8_t *sa = spins_of(st, s, 0, a);
+      int8_t *sb = spins_of(st, s, 1, b);
+      uint32_t M = 0;
+      for (int i = 0; i < N; ++i) {
+        q[i] = (int8_t)(sa[i] * sb[i]); /* Eq. 10 */
+        M += (q[i] == -1);
+      }
+      if (M == 0) continue;
+      int32_t before = *at3(st->E, st, s, 0, a) + *at3(st->E, st, s, 1, b);
+      memset(in, 0, (size_t)N);
+      for (int i0 = 0; i0 < N; ++i0) {
+        if (q[i0] != -1 || in[i0]) continue;
+        /* a new cluster; i0 is its smallest site (sites are visited in increasing order) */
+        int head = 0, tail = 0;
+        queue[tail++] = i0;
+        in[i0] = 1;
+        while (head < tail) {
+          int i = queue[head++];
+          for (int mu = 0; mu < d; ++mu)
+            for (int dir = -1; dir <= 1; dir += 2) {
+              int j = neighbour(st, i, mu, dir);
+              if (!in[j] && q[j] == -1) {
+                in[j] = 1;
+                queue[tail++] = j;
+              }
+            }
+        }
+        uint32_t u = philox_word(st->sim_seed, (uint32_t)i0, t, sg, ((uint32_t)k << 8) | OR_TAG_HMULTI, 0);
+        if (u >> 31) {
+          for (int x = 0; x < tail; ++x) {
+            int i = queue[x];
+            int8_t tmp = sa[i];
+            sa[i] = sb[i];
+            sb[i] = tmp;
+          }
+          st->houd_flipped += (uint64_t)tail;
+        }
+      }
+      int32_t ea = energy(st, s, sa), eb = energy(st, s, sb);
+      if (ea + eb != before) st->error = 2; /* E1 + E2 must be conserved */
+      *at3(st->E, st, s, 0, a) = ea;
+      *at3(st->E, st, s, 1, b) = eb;
+      st->houd_moves++;
+    }
+  }
+  free(q);
+  free(in);
+  free(queue);
+  st->t_houd++;
+}
+
+/* One MCS (Sec. 2.4): n_metro sweeps, one Houdayer move per pair (houdayer = 1: the
+ * single-cluster move, 2: the multi-cluster variant), one PT pass. */
 void or_mcs(or_state *st, int n_mcs, int n_metro, int houdayer) {
   for (int a = 0; a < n_mcs; ++a) {
     or_sweep(st, n_metro);
-    if (houdayer) or_houdayer(st);
+    if (houdayer == 1) or_houdayer(st);
+    else if (houdayer == 2) or_houdayer_multi(st);
     or_exchange(st);
   }
 }
@@ -590,7 +667,8 @@ void or_run_binned(or_state *st, int n_mcs, int n_metro, int houdayer, int pt, i
   int per_bin = n_mcs / n_bins;
   for (int a = 0; a < n_bins * per_bin; ++a) {
     or_sweep(st, n_metro);
-    if (houdayer) or_houdayer(st);
+    if (houdayer == 1) or_houdayer(st);
+    else if (houdayer == 2) or_houdayer_multi(st);
     if (pt) or_exchange(st);
     or_measure(st, Eb, NULL);
     int bin = a / per_bin;

@@ -70,6 +70,9 @@ CASES = [
     ("3d2x2x4_pt", 3, (2, 2, 4), [0.8, 1.2, 1.8, 2.6], 120_000, False, True),
     ("3d2x2x4_pt_houdayer", 3, (2, 2, 4), [0.8, 1.2, 1.8, 2.6], 120_000, True, True),
     ("3d2x2x2_metropolis", 3, (2, 2, 2), [0.6, 1.0, 2.0], 150_000, False, False),
+    # the multi-cluster variant of the move (houdayer = 2)
+    ("2d4x4_pt_multicluster", 2, (4, 4), [0.5, 0.8, 1.2, 1.8], 120_000, 2, True),
+    ("3d2x2x4_pt_multicluster", 3, (2, 2, 4), [0.8, 1.2, 1.8, 2.6], 120_000, 2, True),
 ]
 
 

@@ -10,6 +10,9 @@
   flipped set of every pair is exactly one connected component of the q = -1 sites
   (checked with networkx on the periodic lattice graph).  Over repeated moves on a
   fixed q-field the chosen component is hit with frequency size / M (uniform seed).
+* Multi-cluster variant: E1 + E2 conserved, q unchanged, the flipped set of every pair
+  is a union of whole q = -1 components, and each component is flipped with
+  probability 1/2 (binomial over many components).
 * Replica maps stay mutually inverse permutations.
 * Samples are independent and keyed by their job-wide index: a shard of samples
   evolves exactly as the same samples inside the whole job.
@@ -49,7 +52,8 @@ def forward_neighbour(dims, mu):
     return idx
 
 
-@pytest.mark.parametrize("ndim,dims,houd", [(2, (8, 6), True), (3, (4, 4, 6), True), (3, (2, 4, 2), False)])
+@pytest.mark.parametrize("ndim,dims,houd", [(2, (8, 6), True), (3, (4, 4, 6), True), (3, (2, 4, 2), False),
+                                            (2, (8, 6), 2)])
 def test_gauge_covariance(oracle_mod, ndim, dims, houd):
     temps = geometric_temps(0.5, 2.0, 6)
     a = make(oracle_mod, ndim, dims, 3, 2, temps, coupling_seed=5, sim_seed=8)
@@ -204,3 +208,38 @@ def test_measure_overlap_definition(oracle_mod):
             a, b = perm[smp, 0, k], perm[smp, 1, k]
             assert NQ[smp, k] == int((s[smp, 0, a] * s[smp, 1, b]).sum())
             assert E[smp, 0, k] == En[smp, 0, a] and E[smp, 1, k] == En[smp, 1, b]
+
+
+@pytest.mark.parametrize("ndim,dims", [(2, (8, 8)), (3, (4, 4, 4)), (2, (12, 6))])
+def test_multicluster_move_flips_whole_components_by_coins(oracle_mod, ndim, dims):
+    temps = geometric_temps(0.4, 2.0, 5)
+    o = make(oracle_mod, ndim, dims, 3, 2, temps, sim_seed=17)
+    o.mcs(3)
+    n_comp = n_flip = 0
+    for _ in range(12):
+        before = o.spins()
+        E0 = o.energies()
+        perm, _ = o.perm()
+        o.houdayer_multi()
+        after = o.spins()
+        E1 = o.energies()
+        for s in range(3):
+            for k in range(len(temps)):
+                a, b = perm[s, 0, k], perm[s, 1, k]
+                qneg0 = before[s, 0, a] != before[s, 1, b]
+                np.testing.assert_array_equal(qneg0, after[s, 0, a] != after[s, 1, b])
+                flipped = before[s, 0, a] != after[s, 0, a]
+                np.testing.assert_array_equal(flipped, before[s, 1, b] != after[s, 1, b])
+                assert E0[s, 0, a] + E0[s, 1, b] == E1[s, 0, a] + E1[s, 1, b]
+                assert not (flipped & ~qneg0).any()  # only q = -1 sites change
+                for comp in _q_components(dims, qneg0):
+                    idx = np.array(sorted(comp))
+                    got = flipped[idx]
+                    assert got.all() or not got.any()  # a whole component or none of it
+                    n_comp += 1
+                    n_flip += int(got.all())
+        o.sweep(1)
+    assert o.counters()["error"] == 0
+    assert n_comp > 200
+    p = n_flip / n_comp
+    assert abs(p - 0.5) < 4.5 * math.sqrt(0.25 / n_comp), (n_flip, n_comp)
