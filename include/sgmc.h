@@ -81,7 +81,9 @@ typedef struct {
   uint64_t sim_seed;
   int32_t spin_format;   /* SG_PACKED32: 32 replicas of one site per 32-bit word;
                             SG_INT8: one int8 +-1 per spin (the paper's layout)           */
-  int32_t houdayer;      /* 1: sg_run_mcs performs one Houdayer move per (sample, slot)   */
+  int32_t houdayer;      /* 1: sg_run_mcs performs one Houdayer move per (sample, slot);
+                            2: the multi-cluster variant (sg_houdayer_multi) instead;
+                            nonzero also reserves the bitmap scratch of the split move  */
   int32_t n_metro;       /* Metropolis sweeps per MCS (Sec. 2.4 step 1; usually 1), >= 1  */
   int32_t reserved;      /* must be 0                                                     */
 } sg_params;
@@ -113,9 +115,18 @@ sg_status sg_exchange(sg_handle *h, uintptr_t stream);
  * sites; no move if M = 0).  Needs n_chains == 2. */
 sg_status sg_houdayer(sg_handle *h, uintptr_t stream);
 
+/* Multi-cluster variant of the move (the remedy for idle threads named in Sec. 3): for
+ * every (sample, slot) pair, every q = -1 cluster is exchanged between the two replicas
+ * with probability 1/2, by the top bit of its own Philox word, counter (i_min, t_houd,
+ * sample, slot << 8 | 5) with i_min the cluster's smallest site index (canonical order
+ * x + L0 (y + L1 z)).  Needs n_chains == 2, a handle made with houdayer != 0 (or a
+ * lattice whose bitmaps exceed the single-CTA kernel), and cluster labels that fit one
+ * CTA's shared memory (about 95,000 sites); otherwise SG_EUNSUPPORTED. */
+sg_status sg_houdayer_multi(sg_handle *h, uintptr_t stream);
+
 /* n_mcs Monte Carlo steps (Sec. 2.4): n_metro sweeps, then (if houdayer) one Houdayer
- * move per pair, then one exchange pass.  Identical to the same sequence of the three
- * calls above. */
+ * move per pair (the multi-cluster variant when houdayer == 2), then one exchange pass.
+ * Identical to the same sequence of the calls above. */
 sg_status sg_run_mcs(sg_handle *h, int32_t n_mcs, uintptr_t stream);
 
 /* Observables (Eqs. 3-4) into HOST buffers; synchronises `stream`.

@@ -705,10 +705,14 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *ws, int *total) {
 // Shared-memory bytes of the labelling kernel: Q, run starts, run counts per word, parents
 // (at most N/2 runs), scan space, neighbour rows.
 __host__ __device__ inline int label_smem_bytes(int NBW, int N, int R, int D) {
-  return 4 * (3 * NBW + N / 2 + 32) + ((2 * (D - 1) * R + 7) & ~7);
+  return 4 * (3 * NBW + N / 2 + 32 + (N / 64 + 1)) + ((2 * (D - 1) * R + 7) & ~7);
 }
 
-template <int D, int RW>
+// MULTI: the multi-cluster variant -- every cluster is exchanged by its own coin, the top
+// bit of the Philox word with counter (i_min, t_houd, s, k << 8 | TAG_HMULTI), i_min the
+// cluster's smallest canonical site: the start of its root run (roots are the smallest
+// run of their tree, and a run's start is its smallest site).
+template <int D, int RW, bool MULTI>
 __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSplit hs) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geo g = jb.g;
@@ -722,7 +726,8 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   int32_t *pre = reinterpret_cast<int32_t *>(St + NBW); // runs before each word
   int32_t *par = pre + NBW;
   int32_t *misc = par + g.N / 2; // [0..8] scan space, [16] seed root, [17] size
-  uint16_t *nrow = reinterpret_cast<uint16_t *>(misc + 32); // [D-1][R] next row along y (and z)
+  uint32_t *coin = reinterpret_cast<uint32_t *>(misc + 32); // MULTI: coin bit per run
+  uint16_t *nrow = reinterpret_cast<uint16_t *>(coin + g.N / 64 + 1); // [D-1][R] next row along y (and z)
   const uint32_t *Qp = hs.Qg + ((size_t)s * jb.T + a) * NBW;
   uint32_t *Cp = hs.Cg + ((size_t)s * jb.T + a) * NBW;
   for (int i = tid; i < NBW; i += HLAB_NT) Q[i] = Qp[i];
@@ -751,6 +756,8 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   for (int i = i0; i < i1; ++i) pre[i] = run0 + pre[i] - __popc(St[i]); // runs before word i
   __syncthreads();
   for (int i = tid; i < nruns; i += HLAB_NT) par[i] = i;
+  if (MULTI)
+    for (int i = tid; i < g.N / 64 + 1; i += HLAB_NT) coin[i] = 0u;
   __syncthreads();
 
   // unions: the row's wrap (at the row's first word), and the two runs over each overlap
@@ -783,8 +790,27 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   }
   __syncthreads();
 
+  if (MULTI) {
+    // a coin for every root run: locate its start (the last word whose run count before
+    // it does not exceed the run's number, then the start bit within the word)
+    const uint32_t t_houd = (uint32_t)dv.ctr[CTR_THOUD];
+    const uint32_t c3 = ((uint32_t)dv.slot[((size_t)s * jb.C + 0) * jb.T + a] << 8) | TAG_HMULTI;
+    const uint32_t s_glob = (uint32_t)(jb.s_off + s);
+    for (int i = tid; i < nruns; i += HLAB_NT) {
+      if (par[i] != i) continue;
+      int lo = 0, hi = NBW - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      const int r = lo / RW, x = 32 * (lo - r * RW) + nth_set_bit(St[lo], i - pre[lo]);
+      const uint32_t site = (uint32_t)(r * L0 + x);
+      if (philox10(site, t_houd, s_glob, c3, jb.sk0, jb.sk1).x >> 31) atomicOr(&coin[i >> 5], 1u << (i & 31));
+    }
+  }
   // the seed: the floor(u M / 2^32)-th q = -1 site in canonical order (warp 0)
-  if (warp == 0) {
+  if (!MULTI && warp == 0) {
     const uint32_t t_houd = (uint32_t)dv.ctr[CTR_THOUD];
     const int k = dv.slot[((size_t)s * jb.C + 0) * jb.T + a];
     const uint32_t uu = philox10((uint32_t)k, t_houd, (uint32_t)(jb.s_off + s), TAG_HOUD, jb.sk0, jb.sk1).x;
@@ -816,8 +842,9 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   }
   __syncthreads();
 
-  // the seed's cluster: the runs whose root is the seed's root
-  const int root0 = misc[16];
+  // the seed's cluster: the runs whose root is the seed's root (MULTI: whose root's coin
+  // is 1)
+  const int root0 = MULTI ? -1 : misc[16];
   uint32_t size = 0u;
   for (int i = tid; i < NBW; i += HLAB_NT) {
     const uint32_t w = Q[i];
@@ -830,7 +857,9 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
         const int b = __ffs(seg) - 1;
         seg &= seg - 1u;
         ++id;
-        if (par[id] == root0) c |= ((w + (1u << b)) ^ w) & w;
+        const int rt = par[id];
+        const bool take = MULTI ? ((coin[rt >> 5] >> (rt & 31)) & 1u) != 0u : rt == root0;
+        if (take) c |= ((w + (1u << b)) ^ w) & w;
       }
     }
     Cp[i] = c;
@@ -886,20 +915,23 @@ fill_fn pick_fill_rw(int RW) {
   default: return k_houd_fill<D, 8, SMEM>;
   }
 }
-template <int D>
+template <int D, bool MULTI>
 fill_fn pick_label_rw(int RW) {
   switch (RW) {
-  case 1: return k_houd_label<D, 1>;
-  case 2: return k_houd_label<D, 2>;
-  case 3: return k_houd_label<D, 3>;
-  case 4: return k_houd_label<D, 4>;
-  case 5: return k_houd_label<D, 5>;
-  case 6: return k_houd_label<D, 6>;
-  case 7: return k_houd_label<D, 7>;
-  default: return k_houd_label<D, 8>;
+  case 1: return k_houd_label<D, 1, MULTI>;
+  case 2: return k_houd_label<D, 2, MULTI>;
+  case 3: return k_houd_label<D, 3, MULTI>;
+  case 4: return k_houd_label<D, 4, MULTI>;
+  case 5: return k_houd_label<D, 5, MULTI>;
+  case 6: return k_houd_label<D, 6, MULTI>;
+  case 7: return k_houd_label<D, 7, MULTI>;
+  default: return k_houd_label<D, 8, MULTI>;
   }
 }
-fill_fn pick_label(int d, int RW) { return d == 2 ? pick_label_rw<2>(RW) : pick_label_rw<3>(RW); }
+fill_fn pick_label(int d, int RW, bool multi) {
+  if (d == 2) return multi ? pick_label_rw<2, true>(RW) : pick_label_rw<2, false>(RW);
+  return multi ? pick_label_rw<3, true>(RW) : pick_label_rw<3, false>(RW);
+}
 
 fill_fn pick_fill(int d, int RW, bool in_smem) {
   if (d == 2) return in_smem ? pick_fill_rw<2, true>(RW) : pick_fill_rw<2, false>(RW);
@@ -929,9 +961,9 @@ void fill_shape(const Job &jb, int NBW, int *wpb, int *in_smem, int *smem) {
 cudaError_t prepare_houdayer_kernels(int max_smem) {
   for (int rw = 1; rw <= 8; ++rw) {
     for (int d = 2; d <= 3; ++d) {
-      const void *fns[4] = {(const void *)(d == 2 ? pick_houd<2>(rw) : pick_houd<3>(rw)),
+      const void *fns[5] = {(const void *)(d == 2 ? pick_houd<2>(rw) : pick_houd<3>(rw)),
                             (const void *)pick_fill(d, rw, true), (const void *)pick_fill(d, rw, false),
-                            (const void *)pick_label(d, rw)};
+                            (const void *)pick_label(d, rw, false), (const void *)pick_label(d, rw, true)};
       for (const void *fn : fns) {
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
@@ -941,9 +973,15 @@ cudaError_t prepare_houdayer_kernels(int max_smem) {
   return cudaSuccess;
 }
 
+bool houdayer_labels(const Job &jb) {
+  const int RW = (jb.g.L0 + 31) / 32;
+  return label_smem_bytes(jb.g.R * RW, jb.g.N, jb.g.R, jb.g.d) <= HOUD_SMEM_BUDGET;
+}
+
 // With `scratch` (houdayer_scratch_bytes of the handle's buffer) the split form runs;
 // without it the single-CTA form, whose bitmaps must then fit `smem_limit`.
-cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, cudaStream_t st) {
+cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, bool multi,
+                            cudaStream_t st) {
   const int RW = (jb.g.L0 + 31) / 32;
   const int NBW = jb.g.R * RW;
   if (scratch) {
@@ -959,8 +997,9 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     k_houd_q<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     const int lab = label_smem_bytes(NBW, jb.g.N, jb.g.R, jb.g.d);
     if (lab <= HOUD_SMEM_BUDGET) {
-      pick_label(jb.g.d, RW)<<<(unsigned)pairs, HLAB_NT, (size_t)lab, st>>>(jb, dv, hs);
+      pick_label(jb.g.d, RW, multi)<<<(unsigned)pairs, HLAB_NT, (size_t)lab, st>>>(jb, dv, hs);
     } else {
+      if (multi) return cudaErrorNotSupported;
       // labels beyond the shared-memory budget: grow the seed's cluster row by row
       pick_fill(jb.g.d, RW, hs.in_smem != 0)<<<(unsigned)((pairs + hs.wpb - 1) / hs.wpb), 32 * hs.wpb,
                                                 (size_t)smem, st>>>(jb, dv, hs);
@@ -968,6 +1007,7 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     k_houd_flip<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     return cudaGetLastError();
   }
+  if (multi) return cudaErrorNotSupported; // the multi-cluster variant labels in the split form only
   HoudArgs ha;
   ha.RW = RW;
   ha.NBW = NBW;

@@ -65,7 +65,7 @@ sg_status validate(const sg_params *p) {
   }
   if (!(p->p_plus >= 0.0 && p->p_plus <= 1.0)) return SG_EINVAL;
   if (p->spin_format != SG_PACKED32 && p->spin_format != SG_INT8) return SG_EINVAL;
-  if (p->houdayer != 0 && p->houdayer != 1) return SG_EINVAL;
+  if (p->houdayer < 0 || p->houdayer > 2) return SG_EINVAL;
   if (p->houdayer && p->n_chains != 2) return SG_EINVAL;
   if (p->n_metro < 1 || p->reserved != 0) return SG_EINVAL;
   for (int a = 0; a < p->ndim; ++a)
@@ -262,9 +262,9 @@ sg_status recompute_energy(sg_handle *h, cudaStream_t st) {
 }
 
 // The cluster move itself (spins only; energies are stale until recomputed).
-sg_status houdayer_move(sg_handle *h, cudaStream_t st) {
+sg_status houdayer_move(sg_handle *h, cudaStream_t st, bool multi) {
   uint32_t *scratch = h->lay.houd_bytes ? reinterpret_cast<uint32_t *>(h->buf + h->lay.houd) : nullptr;
-  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, HOUD_SMEM_BUDGET, st));
+  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, HOUD_SMEM_BUDGET, multi, st));
   if (r == SG_OK) h->t_houd += 1;
   return r;
 }
@@ -393,7 +393,23 @@ sg_status sg_houdayer(sg_handle *h, uintptr_t stream) {
   if (h->job.C != 2) return SG_EINVAL;
   if (!houdayer_possible(&h->p, h->job)) return SG_EUNSUPPORTED;
   cudaStream_t st = as_stream(stream);
-  sg_status r = houdayer_move(h, st);
+  sg_status r = houdayer_move(h, st, false);
+  return r == SG_OK ? recompute_energy(h, st) : r;
+}
+
+// The multi-cluster variant needs the bitmap scratch (a handle made with houdayer != 0,
+// or a lattice too large for the single-CTA kernel) and labels that fit shared memory.
+bool multi_possible(const sg_handle *h) {
+  return houdayer_possible(&h->p, h->job) && h->lay.houd_bytes > 0 && houdayer_labels(h->job);
+}
+
+sg_status sg_houdayer_multi(sg_handle *h, uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->job.C != 2) return SG_EINVAL;
+  if (!multi_possible(h)) return SG_EUNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  sg_status r = houdayer_move(h, st, true);
   return r == SG_OK ? recompute_energy(h, st) : r;
 }
 
@@ -412,10 +428,11 @@ sg_status mcs_ops(sg_handle *h, int n_mcs, cudaStream_t st) {
     return r;
   }
   if (h->p.houdayer && !houdayer_possible(&h->p, h->job)) return SG_EUNSUPPORTED;
+  if (h->p.houdayer == 2 && !multi_possible(h)) return SG_EUNSUPPORTED;
   for (int m = 0; m < n_mcs; ++m) {
     sg_status r = sweeps(h, nm, st);
     if (r == SG_OK && h->p.houdayer) {
-      r = houdayer_move(h, st);
+      r = houdayer_move(h, st, h->p.houdayer == 2);
       if (r == SG_OK && h->fuse_pt && !h->global) {
         // energies after the move, then the exchange, in one resident launch
         r = launch_resident<true, true>(h, st, 1, 1);

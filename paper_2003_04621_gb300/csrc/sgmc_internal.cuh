@@ -23,7 +23,7 @@
 namespace sgmc {
 
 // Philox stream tags (the last counter word's low byte).
-constexpr uint32_t TAG_METRO = 0u, TAG_PT = 1u, TAG_HOUD = 2u, TAG_INIT = 3u, TAG_J = 4u;
+constexpr uint32_t TAG_METRO = 0u, TAG_PT = 1u, TAG_HOUD = 2u, TAG_INIT = 3u, TAG_J = 4u, TAG_HMULTI = 5u;
 
 // Counter slots in the device counter array.
 constexpr int CTR_NEAR = 0;   // near-threshold exchange decisions
@@ -342,7 +342,10 @@ cudaError_t static_sweep_scratch(void **ptr);
 cudaError_t launch_global_energy(const Job &jb, const Dev &dv, uint2 *tables, uint32_t *esum, cudaStream_t st);
 int houdayer_smem(const Job &jb, int bitmaps_smem);
 size_t houdayer_scratch_bytes(const Job &jb);
-cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, cudaStream_t st);
+// Whether the labelling kernel (and so the multi-cluster variant) runs for this lattice.
+bool houdayer_labels(const Job &jb);
+cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, bool multi,
+                            cudaStream_t st);
 } // namespace sgmc
 
 namespace sgmc {

@@ -49,8 +49,8 @@ class Params(ctypes.Structure):
 
 
 EXPORTED = (
-    "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_run_mcs", "sg_measure",
-    "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
+    "sg_measure", "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
@@ -75,6 +75,7 @@ def lib():
         "sg_sweep": [P, I32, U],
         "sg_exchange": [P, U],
         "sg_houdayer": [P, U],
+        "sg_houdayer_multi": [P, U],
         "sg_run_mcs": [P, I32, U],
         "sg_measure": [P, P, P, U],
         "sg_measure_device": [P, P, P, U],
@@ -112,7 +113,7 @@ def _check(status: int, where: str):
 
 def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, temps: Sequence[float],
                 coupling_seed: int = 1, sim_seed: int = 1, p_plus: float = 0.5, spin_format: str = "packed",
-                houdayer: bool = False, n_metro: int = 1, sample_offset: int = 0):
+                houdayer=False, n_metro: int = 1, sample_offset: int = 0):
     """Fill an sg_params; returns (params, temps_array) -- keep the array alive."""
     t = np.ascontiguousarray(np.asarray(temps, dtype=np.float64))
     p = Params()
@@ -128,7 +129,7 @@ def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, t
     p.p_plus = float(p_plus)
     p.sim_seed = int(sim_seed)
     p.spin_format = SG_INT8 if spin_format == "int8" else SG_PACKED32
-    p.houdayer = int(bool(houdayer))
+    p.houdayer = 2 if (houdayer is not True and houdayer == 2) else int(bool(houdayer))
     p.n_metro = int(n_metro)
     p.reserved = 0
     return p, t
@@ -209,6 +210,10 @@ class Simulation:
 
     def houdayer(self, stream=None):
         _check(lib().sg_houdayer(self._h, self._s(stream)), "sg_houdayer")
+
+    def houdayer_multi(self, stream=None):
+        """Multi-cluster variant: every q = -1 cluster of a pair exchanged by its own coin."""
+        _check(lib().sg_houdayer_multi(self._h, self._s(stream)), "sg_houdayer_multi")
 
     def run_mcs(self, n: int = 1, stream=None):
         _check(lib().sg_run_mcs(self._h, int(n), self._s(stream)), "sg_run_mcs")

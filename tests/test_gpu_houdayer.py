@@ -4,7 +4,10 @@ Every (sample, temperature slot) pair chooses its seed from its own Philox word 
 floor(u M / 2^32)-th q = -1 site in site order; the cluster is the seed's connected q = -1
 component, grown on the GPU row by row (periodic runs, queue of rows) and by breadth-
 first search in the oracle.  After every step the spins, energies, replica maps, N q and
-the number of flipped sites must be identical.
+the number of flipped sites must be identical.  The multi-cluster variant ("H", or
+houdayer=2 in the MCS) exchanges every q = -1 cluster by its own coin, keyed by the
+cluster's smallest site: the GPU labels all clusters by union-find over row runs, the
+oracle by breadth-first search from each unlabelled site in increasing order.
 """
 import numpy as np
 import pytest
@@ -35,12 +38,15 @@ def run_pair(oracle_mod, kw, ops, check_every=1):
         elif op == "h":
             sim.houdayer()
             orc.houdayer()
+        elif op == "H":
+            sim.houdayer_multi()
+            orc.houdayer_multi()
         elif op == "x":
             sim.exchange()
             orc.exchange()
         elif op == "m":
             sim.run_mcs(1)
-            orc.mcs(1, houdayer=bool(kw.get("houdayer", False)))
+            orc.mcs(1, houdayer=kw.get("houdayer", False))
         if t % check_every == 0 or t == len(ops) - 1:
             assert_same_state(sim, orc, f"step {t} ({op})")
     c = orc.counters()
@@ -133,3 +139,33 @@ def test_houdayer_refused_where_unsupported():
     with pytest.raises(SGError) as e:
         one.houdayer()
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("ndim,dims,T", [(2, (16, 16), 8), (2, (40, 24), 12), (2, (66, 4), 5), (2, (2, 8), 3),
+                                         (3, (8, 8, 8), 12), (3, (4, 6, 2), 32), (3, (16, 4, 8), 5)])
+def test_multicluster_calls(oracle_mod, ndim, dims, T):
+    kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.2, 2.0, T), sim_seed=23,
+              coupling_seed=6, houdayer=2)
+    run_pair(oracle_mod, kw, list("sHxsHhxHs"))
+
+
+def test_multicluster_mcs_2d_l128(oracle_mod):
+    """The 2D L=128 x 24-temperature job with the multi-cluster variant in every MCS."""
+    w = workload_2d_l128_houdayer()
+    kw = dict(ndim=2, dims=w.dims, n_samples=2, n_chains=2, temps=list(w.temps), sim_seed=w.sim_seed,
+              coupling_seed=w.coupling_seed, sample_offset=100, houdayer=2)
+    sim, orc = run_pair(oracle_mod, kw, ["m"] * 5)
+    assert orc.counters()["houd_moves"] > 0
+
+
+def test_multicluster_refused_without_scratch():
+    from paper_2003_04621_gb300.sgmc import SGError
+
+    sim = gpu_of(ndim=2, dims=(8, 8), n_samples=1, n_chains=2, temps=[1.0, 2.0])  # houdayer=0: no scratch
+    with pytest.raises(SGError) as e:
+        sim.houdayer_multi()
+    assert e.value.status == 5
+    big = gpu_of(ndim=2, dims=(256, 3200), n_samples=1, n_chains=2, temps=[1.0, 2.0], houdayer=True)
+    with pytest.raises(SGError) as e:  # labels beyond one CTA's shared memory
+        big.houdayer_multi()
+    assert e.value.status == 5
