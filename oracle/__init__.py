@@ -77,6 +77,7 @@ def _load():
         lib.or_mcs.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         for name in ("or_measure",):
             getattr(lib, name).argtypes = [P, P, P]
+        lib.or_qmodes.argtypes = [P, P]
         lib.or_check_energies.restype = ctypes.c_int
         lib.or_check_energies.argtypes = [P]
         for name in ("or_get_spins", "or_set_spins", "or_get_couplings", "or_set_couplings",
@@ -189,6 +190,13 @@ class Oracle:
         q = np.zeros((self.S, self.T), np.int32)
         self._lib.or_measure(self._h, _ptr(e), _ptr(q) if self.C >= 2 else None)
         return e, (q if self.C >= 2 else None)
+
+    def qmodes(self) -> np.ndarray:
+        """Overlap plane sums P[s][k][mu][x] (int32, x < max extent)."""
+        Lmax = max(self.dims[: self.d])
+        out = np.zeros((self.S, self.T, self.d, Lmax), np.int32)
+        self._lib.or_qmodes(self._h, _ptr(out))
+        return out
 
     def spins(self) -> np.ndarray:
         out = np.zeros((self.S, self.C, self.T, self.N), np.uint8)

@@ -18,6 +18,7 @@
  * What each function follows:
  *   model, couplings             Sec. 2.1, Eq. 1 (H = 0) and Eq. 2 (bimodal, p)
  *   energy, overlap              Sec. 2.1, Eqs. 3-4
+ *   overlap plane sums           Sec. 3 (two-replica measurements), Eq. 4 per plane
  *   Metropolis sweep             Sec. 2.2 / 2.4 step 1 (single-spin flip, Metropolis
  *                                rule), visited in checkerboard order
  *   replica exchange             Sec. 2.2, Eq. 5; temperature<->replica maps as two
@@ -569,6 +570,34 @@ void or_measure(const or_state *st_c, int32_t *E_by_slot, int32_t *NQ) {
         for (int i = 0; i < st->N; ++i) qsum += sa[i] * sb[i];
         NQ[(size_t)s * st->T + k] = qsum;
       }
+}
+
+/* Plane sums of the overlap field, the integer part of the Fourier modes behind the
+ * spin-glass susceptibility and the correlation length (two-replica quantities, Sec. 3):
+ * P[s][k][mu][x] = sum of q_i = s_i^(a) s_i^(b) (Eq. 4 before the sum) over the sites
+ * i with coordinate x along axis mu, a and b the chain-0 and chain-1 replicas at slot
+ * k.  Lmax = max extent; entries x >= L_mu are 0.  Then q(k e_mu) = (1/N) sum_x
+ * e^{i k x} P[mu][x]. */
+void or_qmodes(const or_state *st_c, int32_t *P) {
+  or_state *st = (or_state *)st_c;
+  const int d = st->ndim;
+  int Lmax = st->L[0];
+  for (int mu = 1; mu < d; ++mu)
+    if (st->L[mu] > Lmax) Lmax = st->L[mu];
+  memset(P, 0, sizeof(int32_t) * (size_t)st->S * st->T * d * Lmax);
+  if (st->C < 2) return;
+  for (int s = 0; s < st->S; ++s)
+    for (int k = 0; k < st->T; ++k) {
+      const int8_t *sa = spins_of(st, s, 0, *at3(st->perm, st, s, 0, k));
+      const int8_t *sb = spins_of(st, s, 1, *at3(st->perm, st, s, 1, k));
+      int32_t *Pk = P + ((size_t)s * st->T + k) * d * Lmax;
+      for (int i = 0; i < st->N; ++i) {
+        int c[3];
+        site_coords(st, i, &c[0], &c[1], &c[2]);
+        const int q = sa[i] * sb[i];
+        for (int mu = 0; mu < d; ++mu) Pk[mu * Lmax + c[mu]] += q;
+      }
+    }
 }
 
 /* Recompute every energy from Eq. 1 and report how many differ from the kept ones. */
