@@ -139,6 +139,17 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
 /* As sg_measure, into DEVICE buffers of the same shapes, without synchronising. */
 sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
 
+/* Overlap plane sums, the integer part of the Fourier modes of the overlap field behind
+ * the spin-glass susceptibility and the correlation length (two-replica measurements,
+ * Sec. 3): P_out[s][k][mu][x] = sum of s_i^(a) s_i^(b) (the summand of Eq. 4) over the
+ * sites i with coordinate x along axis mu, a / b the chain-0 / chain-1 replicas at
+ * temperature slot k; x < Lmax = the largest extent, entries x >= L_mu are 0.  Then
+ * q(k e_mu) = (1/N) sum_x exp(i k x) P[mu][x].  Needs n_chains == 2 (else SG_EINVAL).
+ * sg_measure_qmodes writes a host buffer and synchronises the stream;
+ * sg_measure_qmodes_device writes device memory and does not. */
+sg_status sg_measure_qmodes(sg_handle *h, int32_t *P_out, uintptr_t stream);
+sg_status sg_measure_qmodes_device(sg_handle *h, int32_t *P_out, uintptr_t stream);
+
 /* Spins in a plain layout, DEVICE buffers: uint8 [n_samples][n_chains][n_temps][N],
  * indexed by replica j (not slot) and site i, 1 iff s = -1.  Import recomputes the
  * energies. */

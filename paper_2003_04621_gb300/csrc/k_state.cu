@@ -249,6 +249,159 @@ __global__ void __launch_bounds__(OV_NT) k_overlap_packed(Job jb, Dev dv, int tl
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Overlap plane sums (the integer part of the Fourier modes of q behind chi_SG and the
+// correlation length, two-replica measurements of Sec. 3): P[s][k][mu][x] = sum of
+// q_i = s_i^(a) s_i^(b) over the sites with coordinate x along axis mu, a / b the
+// chain-0 / chain-1 replicas at slot k.  Entries x >= L_mu are 0.
+// ---------------------------------------------------------------------------------
+constexpr int QM_NT = 256;
+
+// Packed layout: CTA per (sample, block of 32 slots), lane = slot.  Rows are staged in
+// shared memory a tile at a time (both colour halves of every word plane); warps take
+// rows, walk them by half-column (two sites, one per colour, with known x), and each
+// lane adds its slot's q into its slot's accumulators: x in acc[mu=0], the row sum into
+// acc[1][y] and acc[2][z].  The warps share a slot's accumulators, so the adds are
+// atomic; a slot's accumulators are d Lmax + 1 words apart, so the 32 lanes of a warp
+// hit 32 banks.  With GACC they live in the global output instead.
+template <int D, bool GACC>
+__global__ void __launch_bounds__(QM_NT) k_qmodes_packed(Job jb, Dev dv, int Lmax, int nr, int32_t *P_out) {
+  extern __shared__ __align__(16) uint32_t qm_smem[];
+  const Geo g = jb.g;
+  const int H = g.H, L1 = g.L1, R = g.R;
+  const int nblk = (jb.T + 31) >> 5;
+  const int s = blockIdx.x / nblk, blk = blockIdx.x - s * nblk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blk * 32 + lane;
+  const bool valid = k < jb.T;
+  const int a = valid ? dv.perm[((size_t)s * jb.C + 0) * jb.T + k] : 0;
+  const int b = valid ? dv.perm[((size_t)s * jb.C + 1) * jb.T + k] : 0;
+  const int W = jb.W, la = a & 31, lb = b & 31;
+  const int stride = D * Lmax + 1;
+  uint32_t *tile = qm_smem;                 // [W][2][nr * H]
+  const int tw = 2 * nr * H;                // words per plane in the tile
+  int32_t *acc = GACC ? P_out + ((size_t)s * jb.T + (valid ? k : 0)) * D * Lmax
+                      : reinterpret_cast<int32_t *>(qm_smem + (size_t)W * tw) + lane * stride;
+  const uint32_t *ta0 = tile + (size_t)(a >> 5) * tw, *tb0 = tile + (size_t)(jb.Wc + (b >> 5)) * tw;
+  // warp 0 clears every slot's accumulators (the tile loop's first barrier orders it
+  // before any add)
+  if (warp == 0 && (!GACC || valid))
+    for (int i = 0; i < D * Lmax; ++i) acc[i] = 0;
+  const uint32_t *src = dv.spins + (size_t)s * W * g.N;
+  for (int r0 = 0; r0 < R; r0 += nr) {
+    const int rows = min(nr, R - r0), n = rows * H;
+    __syncthreads();
+    for (int e = threadIdx.x; e < W * 2 * n; e += QM_NT) {
+      const int w = e / (2 * n), rem = e - w * 2 * n, c = rem / n, i = rem - c * n;
+      tile[(size_t)w * tw + c * nr * H + i] = src[(size_t)w * g.N + c * g.Nh + r0 * H + i];
+    }
+    __syncthreads();
+    for (int rr = warp; rr < rows; rr += QM_NT / 32) {
+      const int r = r0 + rr, y = r % L1, z = r / L1, par = (y + z) & 1;
+      int rowsum = 0;
+      for (int kk = 0; kk < H; ++kk) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int i = c * nr * H + rr * H + kk;
+          const int x = 2 * kk + (c ^ par);
+          const int q = 1 - 2 * (int)(((ta0[i] >> la) ^ (tb0[i] >> lb)) & 1u);
+          if (!GACC || valid) atomicAdd(&acc[x], q);
+          rowsum += q;
+        }
+      }
+      if (!GACC || valid) {
+        atomicAdd(&acc[Lmax + y], rowsum);
+        if (D == 3) atomicAdd(&acc[2 * Lmax + z], rowsum);
+      }
+    }
+  }
+  __syncthreads(); // every warp's adds are in before a lane copies its slot out
+  if (!GACC) {
+    if (valid) {
+      int32_t *out = P_out + ((size_t)s * jb.T + k) * D * Lmax;
+      for (int i = 0; i < D * Lmax; ++i) out[i] = acc[i];
+    }
+  }
+}
+
+// int8 layout: CTA per (sample, slot); shared-memory accumulators, atomics per site.
+__global__ void __launch_bounds__(256) k_qmodes_int8(Job jb, Dev dv, int Lmax, int32_t *P_out) {
+  extern __shared__ __align__(16) uint32_t qm_smem[];
+  int32_t *acc = reinterpret_cast<int32_t *>(qm_smem);
+  const Geo g = jb.g;
+  const int d = g.d;
+  const int s = blockIdx.x / jb.T, k = blockIdx.x - s * jb.T;
+  const int a = dv.perm[((size_t)s * jb.C + 0) * jb.T + k];
+  const int b = dv.perm[((size_t)s * jb.C + 1) * jb.T + k];
+  const int8_t *sp = reinterpret_cast<const int8_t *>(dv.spins);
+  const int8_t *pa = sp + ((size_t)s * jb.C + 0) * g.N * jb.Tp + a;
+  const int8_t *pb = sp + ((size_t)s * jb.C + 1) * g.N * jb.Tp + b;
+  for (int i = threadIdx.x; i < d * Lmax; i += blockDim.x) acc[i] = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < g.N; p += blockDim.x) {
+    const SiteGeo sg = site_geo(g, p);
+    const int q = (int)pa[(size_t)p * jb.Tp] * (int)pb[(size_t)p * jb.Tp];
+    atomicAdd(&acc[2 * sg.k + sg.xodd], q);
+    atomicAdd(&acc[Lmax + sg.y], q);
+    if (d == 3) atomicAdd(&acc[2 * Lmax + sg.z], q);
+  }
+  __syncthreads();
+  int32_t *out = P_out + (size_t)blockIdx.x * d * Lmax;
+  for (int i = threadIdx.x; i < d * Lmax; i += blockDim.x) out[i] = acc[i];
+}
+
+// Rows per staged tile (the tile holds every word plane, both colours, about 24 KB) and
+// whether the accumulators fit shared memory (96 KB for 32 lanes).
+void qmodes_shape(const Job &jb, int Lmax, int *nr, size_t *smem, bool *gacc) {
+  const int per_row = jb.W * 2 * jb.g.H * 4;
+  int n = 24 * 1024 / per_row;
+  n = n < 1 ? 1 : (n > jb.g.R ? jb.g.R : n);
+  const size_t accb = (size_t)32 * (jb.g.d * Lmax + 1) * 4;
+  *gacc = accb > 96 * 1024;
+  *nr = n;
+  *smem = (size_t)n * per_row + (*gacc ? 0 : accb);
+}
+
+int qmodes_lmax(const Job &jb) {
+  int m = jb.g.L0;
+  if (jb.g.L1 > m) m = jb.g.L1;
+  if (jb.g.d == 3 && jb.g.L2 > m) m = jb.g.L2;
+  return m;
+}
+
+cudaError_t launch_qmodes(const Job &jb, const Dev &dv, bool int8fmt, int32_t *P_out, cudaStream_t st) {
+  if (jb.C < 2) return cudaErrorInvalidValue;
+  const int Lmax = qmodes_lmax(jb);
+  if (int8fmt) {
+    k_qmodes_int8<<<(unsigned)(jb.S * jb.T), 256, (size_t)jb.g.d * Lmax * 4, st>>>(jb, dv, Lmax, P_out);
+    return cudaGetLastError();
+  }
+  int nr;
+  size_t smem;
+  bool gacc;
+  qmodes_shape(jb, Lmax, &nr, &smem, &gacc);
+  const unsigned grid = (unsigned)(jb.S * ((jb.T + 31) / 32));
+  if (jb.g.d == 2) {
+    if (gacc) k_qmodes_packed<2, true><<<grid, QM_NT, smem, st>>>(jb, dv, Lmax, nr, P_out);
+    else k_qmodes_packed<2, false><<<grid, QM_NT, smem, st>>>(jb, dv, Lmax, nr, P_out);
+  } else {
+    if (gacc) k_qmodes_packed<3, true><<<grid, QM_NT, smem, st>>>(jb, dv, Lmax, nr, P_out);
+    else k_qmodes_packed<3, false><<<grid, QM_NT, smem, st>>>(jb, dv, Lmax, nr, P_out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_state_kernels(int max_smem) {
+  const void *fns[5] = {(const void *)k_qmodes_packed<2, false>, (const void *)k_qmodes_packed<2, true>,
+                        (const void *)k_qmodes_packed<3, false>, (const void *)k_qmodes_packed<3, true>,
+                        (const void *)k_qmodes_int8};
+  for (const void *fn : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 namespace {
 unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 } // namespace

@@ -15,7 +15,7 @@ using namespace sgmc;
 namespace {
 
 struct Layout {
-  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, gtab, esum, houd, houd_bytes, total;
+  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, meas_P, gtab, esum, houd, houd_bytes, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -132,6 +132,7 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   L.ctr = take((size_t)(CTR_PT + T) * 8);
   L.meas_E = take(S * C * T * 4);
   L.meas_Q = take(S * T * 4);
+  L.meas_P = take(C >= 2 ? S * T * (size_t)g.d * (size_t)qmodes_lmax(jb) * 4 : 0);
   // streaming sweep path: lane-pair threshold tables and per-replica bond sums
   L.gtab = take(S * (size_t)jb.W * 256 * 8);
   L.esum = take(S * (size_t)jb.W * 32 * 4);
@@ -169,6 +170,7 @@ cudaError_t prepare_device() {
   const int ms = max_dyn_smem();
   e = prepare_resident_kernels(ms);
   if (e == cudaSuccess) e = prepare_houdayer_kernels(ms);
+  if (e == cudaSuccess) e = prepare_state_kernels(ms);
   if (e == cudaSuccess && dev < 64) prepared[dev] = true;
   return e;
 }
@@ -671,6 +673,27 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
   const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
   cudaError_t e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  return poll_device_error(h, st);
+}
+
+sg_status sg_measure_qmodes_device(sg_handle *h, int32_t *P_out, uintptr_t stream) {
+  if (!h || !P_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->job.C < 2) return SG_EINVAL;
+  return check(h, launch_qmodes(h->job, h->dev, h->int8fmt != 0, P_out, as_stream(stream)));
+}
+
+sg_status sg_measure_qmodes(sg_handle *h, int32_t *P_out, uintptr_t stream) {
+  if (!h || !P_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->job.C < 2) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  int32_t *dP = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_P);
+  sg_status r = sg_measure_qmodes_device(h, dP, stream);
+  if (r != SG_OK) return r;
+  const size_t n = (size_t)h->job.S * h->job.T * h->job.g.d * (size_t)qmodes_lmax(h->job);
+  const cudaError_t e = cudaMemcpyAsync(P_out, dP, n * 4, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return check(h, e);
   return poll_device_error(h, st);
 }

@@ -356,4 +356,8 @@ cudaError_t launch_export_couplings(const Job &jb, const Dev &dv, int8_t *out, c
 cudaError_t launch_import_couplings(const Job &jb, const Dev &dv, const int8_t *in, cudaStream_t st);
 cudaError_t launch_measure(const Job &jb, const Dev &dv, bool int8fmt, int32_t *E_out, int32_t *Q_out,
                            cudaStream_t st);
+// Overlap plane sums [S][T][d][Lmax] (Lmax = qmodes_lmax); needs C >= 2.
+int qmodes_lmax(const Job &jb);
+cudaError_t launch_qmodes(const Job &jb, const Dev &dv, bool int8fmt, int32_t *P_out, cudaStream_t st);
+cudaError_t prepare_state_kernels(int max_smem);
 } // namespace sgmc

@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
 
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
-    "sg_measure", "sg_measure_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
@@ -79,6 +79,8 @@ def lib():
         "sg_run_mcs": [P, I32, U],
         "sg_measure": [P, P, P, U],
         "sg_measure_device": [P, P, P, U],
+        "sg_measure_qmodes": [P, P, U],
+        "sg_measure_qmodes_device": [P, P, U],
         "sg_export_spins": [P, P, U],
         "sg_import_spins": [P, P, U],
         "sg_export_couplings": [P, P, U],
@@ -247,6 +249,17 @@ class Simulation:
         """As measure, into torch int32 device tensors; does not synchronise."""
         _check(lib().sg_measure_device(self._h, E_out.data_ptr(), Q_out.data_ptr() if Q_out is not None else None,
                                        self._s(stream)), "sg_measure_device")
+
+    def qmodes(self, stream=None):
+        """Overlap plane sums P[s][k][mu][x] (numpy int32, x < the largest extent); the
+        integer part of the Fourier modes of q (see observables.q_modes).  Synchronises."""
+        out = np.zeros((self.S, self.T, self.ndim, max(self.dims)), np.int32)
+        _check(lib().sg_measure_qmodes(self._h, out.ctypes.data, self._s(stream)), "sg_measure_qmodes")
+        return out
+
+    def qmodes_device(self, P_out, stream=None):
+        """As qmodes, into an int32 device tensor [S][T][d][Lmax]; does not synchronise."""
+        _check(lib().sg_measure_qmodes_device(self._h, P_out.data_ptr(), self._s(stream)), "sg_measure_qmodes_device")
 
     def spins(self, stream=None):
         """uint8 device tensor [S][C][T][N], 1 iff the spin is -1 (replica order)."""
