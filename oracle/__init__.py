@@ -78,6 +78,7 @@ def _load():
         for name in ("or_measure",):
             getattr(lib, name).argtypes = [P, P, P]
         lib.or_qmodes.argtypes = [P, P]
+        lib.or_get_trips.argtypes = [P, P, P]
         lib.or_check_energies.restype = ctypes.c_int
         lib.or_check_energies.argtypes = [P]
         for name in ("or_get_spins", "or_set_spins", "or_get_couplings", "or_set_couplings",
@@ -190,6 +191,13 @@ class Oracle:
         q = np.zeros((self.S, self.T), np.int32)
         self._lib.or_measure(self._h, _ptr(e), _ptr(q) if self.C >= 2 else None)
         return e, (q if self.C >= 2 else None)
+
+    def trips(self):
+        """(round trips completed [S][C] uint32, their total duration [S][C] uint64)."""
+        n = np.zeros((self.S, self.C), np.uint32)
+        tot = np.zeros((self.S, self.C), np.uint64)
+        self._lib.or_get_trips(self._h, _ptr(n), _ptr(tot))
+        return n, tot
 
     def qmodes(self) -> np.ndarray:
         """Overlap plane sums P[s][k][mu][x] (int32, x < max extent)."""

@@ -26,6 +26,7 @@
  *   Houdayer move                Sec. 2.4, Eq. 10 and the text after it
  *   multi-cluster variant        Sec. 3 (every cluster exchanged with probability 1/2)
  *   MCS composition              Sec. 2.4 (Metropolis, then Houdayer, then PT)
+ *   round trips in temperature   Sec. 2.3 (tunnelling time), counted after each pass
  *   random numbers               counter-based Philox (Sec. 3, Salmon et al. 2011)
  *   exact enumeration            brute force over all 2^N states (a pin, not a method
  *                                of the paper)
@@ -145,6 +146,11 @@ typedef struct {
   uint64_t *cls_tries; /* [T][d+1] */
   uint64_t *cls_acc;   /* [T][d+1] */
   uint64_t houd_moves, houd_flipped; /* moves with M > 0, total cluster sites    */
+  /* Round trips in temperature (the tunnelling time of Sec. 2.3), per replica j:   */
+  int8_t *trip_dir;    /* [S][C][T] 0: no extreme seen, 1: bottom last, 2: top last */
+  uint32_t *trip_t0;   /* [S][C][T] exchange pass of the trip's arrival at the bottom */
+  uint32_t *trip_n;    /* [S][C] round trips completed                                */
+  uint64_t *trip_sum;  /* [S][C] their total duration, in exchange passes             */
   int error;                         /* set if an internal consistency check fails */
 } or_state;
 
@@ -253,6 +259,10 @@ or_state *or_create(const or_params *p) {
   st->perm = (int32_t *)malloc(sizeof(int32_t) * ((size_t)S * C * T + 1));
   st->slot = (int32_t *)malloc(sizeof(int32_t) * ((size_t)S * C * T + 1));
   st->pt_accept = (uint64_t *)calloc((size_t)T, sizeof(uint64_t));
+  st->trip_dir = (int8_t *)calloc((size_t)S * C * T + 1, 1);
+  st->trip_t0 = (uint32_t *)calloc((size_t)S * C * T + 1, sizeof(uint32_t));
+  st->trip_n = (uint32_t *)calloc((size_t)S * C + 1, sizeof(uint32_t));
+  st->trip_sum = (uint64_t *)calloc((size_t)S * C + 1, sizeof(uint64_t));
   st->pt_tries = (uint64_t *)calloc((size_t)T, sizeof(uint64_t));
   st->cls_tries = (uint64_t *)calloc((size_t)T * (d + 1), sizeof(uint64_t));
   st->cls_acc = (uint64_t *)calloc((size_t)T * (d + 1), sizeof(uint64_t));
@@ -308,6 +318,10 @@ void or_destroy(or_state *st) {
   free(st->pt_tries);
   free(st->cls_tries);
   free(st->cls_acc);
+  free(st->trip_dir);
+  free(st->trip_t0);
+  free(st->trip_n);
+  free(st->trip_sum);
   free(st);
 }
 
@@ -386,9 +400,39 @@ void or_exchange(or_state *st) {
           slot[b] = k;
         }
       }
+      /* Round trips (Sec. 2.3: the time to go from the lowest to the highest
+       * temperature and back): after pass t + 1, a replica at the lowest slot whose
+       * last extreme was the highest completes a trip that began at its previous
+       * arrival at the bottom; at the highest slot it turns around. */
+      if (st->T >= 2) {
+        const size_t cb = ((size_t)s * st->C + c) * st->T;
+        for (int j = 0; j < st->T; ++j) {
+          int8_t *dir = &st->trip_dir[cb + j];
+          uint32_t *t0 = &st->trip_t0[cb + j];
+          if (slot[j] == 0) {
+            if (*dir == 2) {
+              st->trip_n[(size_t)s * st->C + c]++;
+              st->trip_sum[(size_t)s * st->C + c] += (uint64_t)(t + 1 - *t0);
+              *t0 = t + 1;
+              *dir = 1;
+            } else if (*dir == 0) {
+              *t0 = t + 1;
+              *dir = 1;
+            }
+          } else if (slot[j] == st->T - 1 && *dir == 1) {
+            *dir = 2;
+          }
+        }
+      }
     }
   }
   st->t_pt++;
+}
+
+/* Round-trip counters per chain: n[S][C] trips completed, sum[S][C] total duration. */
+void or_get_trips(const or_state *st, uint32_t *n, uint64_t *sum) {
+  memcpy(n, st->trip_n, sizeof(uint32_t) * (size_t)st->S * st->C);
+  memcpy(sum, st->trip_sum, sizeof(uint64_t) * (size_t)st->S * st->C);
 }
 
 /* ------------------------------------------------------------------------------ */

@@ -54,3 +54,10 @@ def xi_second_moment(chi0: float, chik: float, L: int) -> float:
     kmin = 2.0 * math.pi / L
     r = chi0 / chik - 1.0
     return math.sqrt(max(r, 0.0)) / (2.0 * math.sin(kmin / 2.0))
+
+
+def tunnelling_time(n_trips: np.ndarray, total: np.ndarray) -> float:
+    """Mean round-trip time in temperature (Sec. 2.3: lowest -> highest -> lowest), in
+    exchange passes, from the per-chain trip counters; nan if no trip has completed."""
+    n = float(np.sum(np.asarray(n_trips, dtype=np.float64)))
+    return float(np.sum(np.asarray(total, dtype=np.float64))) / n if n > 0 else float("nan")
