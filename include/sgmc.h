@@ -85,7 +85,8 @@ typedef struct {
                             2: the multi-cluster variant (sg_houdayer_multi) instead;
                             nonzero also reserves the bitmap scratch of the split move  */
   int32_t n_metro;       /* Metropolis sweeps per MCS (Sec. 2.4 step 1; usually 1), >= 1  */
-  int32_t reserved;      /* must be 0                                                     */
+  int32_t track_trips;   /* 1: count round trips in temperature after every exchange
+                            pass (the tunnelling time of Sec. 2.3; see sg_trips); 0: off */
 } sg_params;
 
 /* Bytes of device memory a handle with these parameters needs. */
@@ -138,6 +139,14 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
 
 /* As sg_measure, into DEVICE buffers of the same shapes, without synchronising. */
 sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
+
+/* Round trips in temperature (Sec. 2.3: lowest -> highest -> lowest), counted after
+ * every exchange pass t = 1, 2, ...: a replica at the lowest slot whose last extreme was
+ * the highest completes a trip that began at its previous arrival at the lowest slot.
+ * n_out[s][c] = trips completed in chain c of sample s, sum_out[s][c] = their total
+ * duration in passes (host buffers; synchronises).  SG_EINVAL unless the handle was
+ * made with track_trips = 1. */
+sg_status sg_trips(sg_handle *h, uint32_t *n_out, uint64_t *sum_out, uintptr_t stream);
 
 /* Overlap plane sums, the integer part of the Fourier modes of the overlap field behind
  * the spin-glass susceptibility and the correlation length (two-replica measurements,

@@ -229,6 +229,11 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   auto UW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 384); };
   auto NEAR = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 448); };
   auto SLOW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 449); };
+  auto TD = [&](int ci) { return ptw + ci * PT_WORDS + 452; };
+  auto T0 = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 516); };
+  auto TN = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 580); };
+  auto TSUM = [&](int ci) { return reinterpret_cast<unsigned long long *>(ptw + ci * PT_WORDS + 582); };
+  const bool track = dv.trip_dir != nullptr;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -280,8 +285,16 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       PM(warp)[j] = j < jb.T ? dv.perm[cb + j] : 0;
       SL(warp)[j] = j < jb.T ? dv.slot[cb + j] : 0;
       PACC(warp)[j] = 0u;
+      if (track) {
+        TD(warp)[j] = j < jb.T ? dv.trip_dir[cb + j] : 0;
+        T0(warp)[j] = j < jb.T ? dv.trip_t0[cb + j] : 0u;
+      }
     }
-    if (lane == 0) *NEAR(warp) = 0u;
+    if (lane == 0) {
+      *NEAR(warp) = 0u;
+      *TN(warp) = 0u;
+      *TSUM(warp) = 0ull;
+    }
   }
   const bool ok = mbar_wait(bar, 0, MBAR_MAX_TRIES);
   if (__syncthreads_or(!ok)) {
@@ -334,6 +347,28 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), ACCB(warp), REJB(warp), UW(warp),
                             PACC(warp), NEAR(warp), SLOW(warp), s_glob, (uint32_t)(c0 + warp),
                             t_pt0 + (uint32_t)m, jb);
+        if (track) {
+          uint32_t n_add = 0u;
+          unsigned long long sum_add = 0ull;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < jb.T) {
+              int32_t dir = TD(warp)[j];
+              uint32_t t0 = T0(warp)[j];
+              trip_step(jb.T, SL(warp)[j], dir, t0, t_pt0 + (uint32_t)m + 1u, n_add, sum_add);
+              TD(warp)[j] = dir;
+              T0(warp)[j] = t0;
+            }
+          }
+          n_add = __reduce_add_sync(FULL, n_add);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sum_add += __shfl_xor_sync(FULL, sum_add, o);
+          if (lane == 0) {
+            *TN(warp) += n_add;
+            *TSUM(warp) += sum_add;
+          }
+        }
         if (!ENERGY_ONLY) {
           for (int wc = 0; wc < jb.Wc; ++wc) {
             const int nv = min(32, jb.T - wc * 32);
@@ -357,8 +392,17 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         dv.slot[cb + j] = SL(warp)[j];
       }
       if (j + 1 < jb.T && PACC(warp)[j]) atomicAdd(&dv.ctr[CTR_PT + j], (unsigned long long)PACC(warp)[j]);
+      if (track && j < jb.T) {
+        dv.trip_dir[cb + j] = TD(warp)[j];
+        dv.trip_t0[cb + j] = T0(warp)[j];
+      }
     }
     if (lane == 0 && *NEAR(warp)) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*NEAR(warp));
+    if (track && lane == 0) {
+      const size_t chain = (size_t)s * jb.C + c0 + warp;
+      dv.trip_n[chain] += *TN(warp);
+      dv.trip_sum[chain] += *TSUM(warp);
+    }
   }
   if (!ENERGY_ONLY) {
     fence_proxy_async(); // this thread's shared-memory writes -> visible to the TMA store
@@ -511,9 +555,11 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
       }
     }
     if (FUSE_PT) {
-      if (tid == 0)
+      if (tid == 0) {
         exchange_chain(T, dv.beta, pm, sl, eacc, s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb.sk0, jb.sk1,
                        [&](int k) { pacc[k] += 1u; }, [&]() { *pnear += 1u; });
+        trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
+      }
       __syncthreads();
       if (!ENERGY_ONLY)
         for (int j = tid; j < T; j += NT)
@@ -552,6 +598,7 @@ __global__ void k_exchange(Job jb, Dev dv) {
     exchange_chain(jb.T, dv.beta, dv.perm + base, dv.slot + base, dv.E + base, (uint32_t)(jb.s_off + s),
                    (uint32_t)c, t_pt, jb.sk0, jb.sk1, [&](int k) { atomicAdd(&ctr[CTR_PT + k], 1ull); },
                    [&]() { atomicAdd(&ctr[CTR_NEAR], 1ull); });
+    trip_chain(dv, (size_t)chain, jb.T, dv.slot + base, t_pt + 1u);
   }
   grid_done_advance(dv.ctr, 0ull, 1ull, 0ull);
 }
@@ -678,6 +725,7 @@ __global__ void k_exchange_batch(const __grid_constant__ ResidentParams<MAX_BATC
     exchange_chain(jb.T, dv.beta, dv.perm + base, dv.slot + base, dv.E + base, (uint32_t)(jb.s_off + s),
                    (uint32_t)c, t_pt, jb.sk0, jb.sk1, [&](int k) { atomicAdd(&ctr[CTR_PT + k], 1ull); },
                    [&]() { atomicAdd(&ctr[CTR_NEAR], 1ull); });
+    trip_chain(dv, (size_t)chain, jb.T, dv.slot + base, t_pt + 1u);
   }
   job_done_advance(dv.ctr, JD.n_items, 0ull, 1ull, 0ull);
 }

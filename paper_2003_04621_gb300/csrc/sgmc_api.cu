@@ -15,7 +15,8 @@ using namespace sgmc;
 namespace {
 
 struct Layout {
-  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, meas_P, gtab, esum, houd, houd_bytes, total;
+  size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, meas_P, gtab, esum, houd, houd_bytes;
+  size_t trip_dir, trip_t0, trip_n, trip_sum, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -67,7 +68,7 @@ sg_status validate(const sg_params *p) {
   if (p->spin_format != SG_PACKED32 && p->spin_format != SG_INT8) return SG_EINVAL;
   if (p->houdayer < 0 || p->houdayer > 2) return SG_EINVAL;
   if (p->houdayer && p->n_chains != 2) return SG_EINVAL;
-  if (p->n_metro < 1 || p->reserved != 0) return SG_EINVAL;
+  if (p->n_metro < 1 || (p->track_trips != 0 && p->track_trips != 1)) return SG_EINVAL;
   for (int a = 0; a < p->ndim; ++a)
     if (p->dims[a] % 2) return SG_EUNSUPPORTED; // checkerboard needs even extents
   return SG_OK;
@@ -142,6 +143,12 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   if (houdayer_possible(p, jb) && (p->houdayer || houdayer_smem(jb, 1) > HOUD_SMEM_BUDGET))
     L.houd_bytes = houdayer_scratch_bytes(jb);
   L.houd = take(L.houd_bytes);
+  // round trips in temperature, when tracked
+  const size_t tr = p->track_trips ? 1 : 0;
+  L.trip_dir = take(tr * S * C * T * 4);
+  L.trip_t0 = take(tr * S * C * T * 4);
+  L.trip_n = take(tr * S * C * 4);
+  L.trip_sum = take(tr * S * C * 8);
   L.total = off;
   return L;
 }
@@ -350,6 +357,11 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   dv.thr = reinterpret_cast<const uint32_t *>(h->buf + h->lay.thr);
   dv.beta = reinterpret_cast<const double *>(h->buf + h->lay.beta);
   dv.ctr = reinterpret_cast<unsigned long long *>(h->buf + h->lay.ctr);
+  const bool tr = p->track_trips != 0;
+  dv.trip_dir = tr ? reinterpret_cast<int32_t *>(h->buf + h->lay.trip_dir) : nullptr;
+  dv.trip_t0 = tr ? reinterpret_cast<uint32_t *>(h->buf + h->lay.trip_t0) : nullptr;
+  dv.trip_n = tr ? reinterpret_cast<uint32_t *>(h->buf + h->lay.trip_n) : nullptr;
+  dv.trip_sum = tr ? reinterpret_cast<unsigned long long *>(h->buf + h->lay.trip_sum) : nullptr;
 
   cudaStream_t st = as_stream(stream);
   cudaError_t e = prepare_device();
@@ -358,6 +370,7 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->buf + h->lay.beta, h->beta.data(), h->beta.size() * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dv.ctr, 0, (size_t)h->n_ctr * 8, st);
+  if (e == cudaSuccess && tr) e = cudaMemsetAsync(h->buf + h->lay.trip_dir, 0, h->lay.total - h->lay.trip_dir, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf + h->lay.esum, 0, (size_t)h->job.S * h->job.W * 32 * 4, st);
   if (e == cudaSuccess) e = launch_init(h->job, dv, h->int8fmt != 0, st);
   if (e != cudaSuccess) {
@@ -673,6 +686,18 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
   const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
   cudaError_t e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  return poll_device_error(h, st);
+}
+
+sg_status sg_trips(sg_handle *h, uint32_t *n_out, uint64_t *sum_out, uintptr_t stream) {
+  if (!h || !n_out || !sum_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (!h->dev.trip_n) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  const size_t n = (size_t)h->job.S * h->job.C;
+  cudaError_t e = cudaMemcpyAsync(n_out, h->dev.trip_n, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sum_out, h->dev.trip_sum, n * 8, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return check(h, e);
   return poll_device_error(h, st);
 }

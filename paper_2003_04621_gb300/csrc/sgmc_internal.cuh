@@ -72,7 +72,51 @@ struct Dev {
   const uint32_t *thr;
   const double *beta;
   unsigned long long *ctr;
+  // round trips in temperature (null when the job does not track them)
+  int32_t *trip_dir;             // [S][C][T] 0: no extreme yet, 1: lowest slot last, 2: highest last
+  uint32_t *trip_t0;             // [S][C][T] exchange pass of the trip's arrival at the lowest slot
+  uint32_t *trip_n;              // [S][C] round trips completed
+  unsigned long long *trip_sum;  // [S][C] their total duration in exchange passes
 };
+
+// Round-trip bookkeeping of one replica after exchange pass t (counted from 1) (the
+// tunnelling time of Sec. 2.3: lowest -> highest -> lowest temperature): at the lowest
+// slot a replica whose last extreme was the highest completes a trip that began at its
+// previous arrival at the bottom; at the highest slot it turns around.
+__device__ __forceinline__ void trip_step(int T, int k, int32_t &dir, uint32_t &t0, uint32_t t, uint32_t &n_add,
+                                          unsigned long long &sum_add) {
+  if (T < 2) return;
+  if (k == 0) {
+    if (dir == 2) {
+      n_add += 1u;
+      sum_add += (unsigned long long)(t - t0);
+      t0 = t;
+      dir = 1;
+    } else if (dir == 0) {
+      t0 = t;
+      dir = 1;
+    }
+  } else if (k == T - 1 && dir == 1) {
+    dir = 2;
+  }
+}
+
+// The same for every replica of one chain, by one thread, in global memory.
+__device__ __forceinline__ void trip_chain(const Dev &dv, size_t chain, int T, const int32_t *slot, uint32_t t) {
+  if (!dv.trip_dir) return;
+  const size_t cb = chain * (size_t)T;
+  uint32_t n_add = 0u;
+  unsigned long long sum_add = 0ull;
+  for (int j = 0; j < T; ++j) {
+    int32_t dir = dv.trip_dir[cb + j];
+    uint32_t t0 = dv.trip_t0[cb + j];
+    trip_step(T, slot[j], dir, t0, t, n_add, sum_add);
+    dv.trip_dir[cb + j] = dir;
+    dv.trip_t0[cb + j] = t0;
+  }
+  dv.trip_n[chain] += n_add;
+  dv.trip_sum[chain] += sum_add;
+}
 
 // One job of a resident-kernel launch: its description, the CTAs it owns (a contiguous
 // range of the grid), whether its exchange runs inside the kernel, and its sweeps per MCS.
@@ -284,7 +328,9 @@ __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 // Shared-memory map of the resident packed kernel: `wpc` 32-replica word lattices of one
 // sample, its expanded couplings, per-lane threshold tables, energy partial sums and the
 // per-chain exchange scratch.
-constexpr int PT_WORDS = 7 * 64 + 4; // per chain (<= 64 replicas): perm, slot, E, accepts, bounds, u; flags
+// per chain (<= 64 replicas): perm, slot, E, accepts, bounds, u; flags; round-trip
+// state (direction, start) and counters
+constexpr int PT_WORDS = 9 * 64 + 8;
 struct PackedSmem {
   int spin, jbyte, jpl, thr, epart, pt, bar, total;
 };

@@ -44,13 +44,13 @@ class Params(ctypes.Structure):
         ("spin_format", ctypes.c_int32),
         ("houdayer", ctypes.c_int32),
         ("n_metro", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("track_trips", ctypes.c_int32),
     ]
 
 
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
-    "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
@@ -80,6 +80,7 @@ def lib():
         "sg_measure": [P, P, P, U],
         "sg_measure_device": [P, P, P, U],
         "sg_measure_qmodes": [P, P, U],
+        "sg_trips": [P, P, P, U],
         "sg_measure_qmodes_device": [P, P, U],
         "sg_export_spins": [P, P, U],
         "sg_import_spins": [P, P, U],
@@ -115,7 +116,7 @@ def _check(status: int, where: str):
 
 def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, temps: Sequence[float],
                 coupling_seed: int = 1, sim_seed: int = 1, p_plus: float = 0.5, spin_format: str = "packed",
-                houdayer=False, n_metro: int = 1, sample_offset: int = 0):
+                houdayer=False, n_metro: int = 1, sample_offset: int = 0, track_trips: bool = False):
     """Fill an sg_params; returns (params, temps_array) -- keep the array alive."""
     t = np.ascontiguousarray(np.asarray(temps, dtype=np.float64))
     p = Params()
@@ -133,7 +134,7 @@ def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, t
     p.spin_format = SG_INT8 if spin_format == "int8" else SG_PACKED32
     p.houdayer = 2 if (houdayer is not True and houdayer == 2) else int(bool(houdayer))
     p.n_metro = int(n_metro)
-    p.reserved = 0
+    p.track_trips = int(bool(track_trips))
     return p, t
 
 
@@ -156,7 +157,7 @@ class Simulation:
 
     def __init__(self, ndim, dims, n_samples, n_chains, temps, coupling_seed=1, sim_seed=1, p_plus=0.5,
                  spin_format="packed", houdayer=False, n_metro=1, sample_offset=0, stream=None, device=None,
-                 device_buffer=None):
+                 device_buffer=None, track_trips=False):
         """device_buffer: optional (device pointer, bytes) the job lives in (256-byte
         aligned, at least query_bytes); by default a torch buffer is allocated."""
         import torch
@@ -169,7 +170,8 @@ class Simulation:
         self.N = int(np.prod(self.dims))
         self.S, self.C, self.T = int(n_samples), int(n_chains), len(temps)
         self.params, self._temps = make_params(ndim, dims, n_samples, n_chains, temps, coupling_seed, sim_seed,
-                                               p_plus, spin_format, houdayer, n_metro, sample_offset)
+                                               p_plus, spin_format, houdayer, n_metro, sample_offset,
+                                               track_trips)
         self.bytes = query_bytes(self.params)
         if device_buffer is not None:
             self._buf = None
@@ -249,6 +251,14 @@ class Simulation:
         """As measure, into torch int32 device tensors; does not synchronise."""
         _check(lib().sg_measure_device(self._h, E_out.data_ptr(), Q_out.data_ptr() if Q_out is not None else None,
                                        self._s(stream)), "sg_measure_device")
+
+    def trips(self, stream=None):
+        """(round trips completed [S][C] uint32, their total duration [S][C] uint64), in
+        exchange passes (needs track_trips=True at creation).  Synchronises."""
+        n = np.zeros((self.S, self.C), np.uint32)
+        tot = np.zeros((self.S, self.C), np.uint64)
+        _check(lib().sg_trips(self._h, n.ctypes.data, tot.ctypes.data, self._s(stream)), "sg_trips")
+        return n, tot
 
     def qmodes(self, stream=None):
         """Overlap plane sums P[s][k][mu][x] (numpy int32, x < the largest extent); the
