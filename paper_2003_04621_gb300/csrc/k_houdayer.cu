@@ -632,18 +632,20 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_flip(Job jb, Dev dv, HoudSpl
 // ---------------------------------------------------------------------------------
 constexpr int HLAB_NT = 256;
 
-__device__ __forceinline__ int uf_find(volatile int32_t *par, int x) {
+// Parents are 16-bit run numbers (a pair has at most N/2 <= 65536 runs), which halves the
+// forest's shared memory and lets more CTAs share an SM.
+__device__ __forceinline__ int uf_find(volatile uint16_t *par, int x) {
   for (;;) {
     const int p = par[x];
     if (p == x) return x;
     const int q = par[p];
     if (q == p) return p;
-    par[x] = q; // path halving: q is an ancestor of x
+    par[x] = (uint16_t)q; // path halving: q is an ancestor of x
     x = q;
   }
 }
 
-__device__ __forceinline__ void uf_union(volatile int32_t *par, int a, int b) {
+__device__ __forceinline__ void uf_union(volatile uint16_t *par, int a, int b) {
   for (;;) {
     a = uf_find(par, a);
     b = uf_find(par, b);
@@ -653,7 +655,7 @@ __device__ __forceinline__ void uf_union(volatile int32_t *par, int a, int b) {
       a = b;
       b = t;
     }
-    const int old = atomicCAS(const_cast<int32_t *>(par) + b, b, a);
+    const int old = atomicCAS(const_cast<unsigned short *>(par) + b, (unsigned short)b, (unsigned short)a);
     if (old == b) return;
     b = old; // b was linked meanwhile: continue from its new parent (smaller than b)
   }
@@ -702,10 +704,10 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *ws, int *total) {
   return ex;
 }
 
-// Shared-memory bytes of the labelling kernel: Q, run starts, run counts per word, parents
-// (at most N/2 runs), scan space, neighbour rows.
+// Shared-memory bytes of the labelling kernel: Q, run starts, run counts per word, scan
+// space, coin bits, 16-bit parents (at most N/2 runs), neighbour rows.
 __host__ __device__ inline int label_smem_bytes(int NBW, int N, int R, int D) {
-  return 4 * (3 * NBW + N / 2 + 32 + (N / 64 + 1)) + ((2 * (D - 1) * R + 7) & ~7);
+  return 4 * (3 * NBW + 32 + (N / 64 + 1)) + ((2 * (N / 2) + 7) & ~7) + ((2 * (D - 1) * R + 7) & ~7);
 }
 
 // MULTI: the multi-cluster variant -- every cluster is exchanged by its own coin, the top
@@ -724,10 +726,10 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   uint32_t *Q = reinterpret_cast<uint32_t *>(smem);
   uint32_t *St = Q + NBW;
   int32_t *pre = reinterpret_cast<int32_t *>(St + NBW); // runs before each word
-  int32_t *par = pre + NBW;
-  int32_t *misc = par + g.N / 2; // [0..8] scan space, [16] seed root, [17] size
+  int32_t *misc = pre + NBW; // [0..8] scan space, [16] seed root, [17] size
   uint32_t *coin = reinterpret_cast<uint32_t *>(misc + 32); // MULTI: coin bit per run
-  uint16_t *nrow = reinterpret_cast<uint16_t *>(coin + g.N / 64 + 1); // [D-1][R] next row along y (and z)
+  uint16_t *par = reinterpret_cast<uint16_t *>(coin + g.N / 64 + 1); // union-find parents, by run
+  uint16_t *nrow = par + ((g.N / 2 + 3) & ~3); // [D-1][R] next row along y (and z)
   const uint32_t *Qp = hs.Qg + ((size_t)s * jb.T + a) * NBW;
   uint32_t *Cp = hs.Cg + ((size_t)s * jb.T + a) * NBW;
   for (int i = tid; i < NBW; i += HLAB_NT) Q[i] = Qp[i];
@@ -755,14 +757,14 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   const int run0 = cta_exclusive_scan(nst, misc, &nruns);
   for (int i = i0; i < i1; ++i) pre[i] = run0 + pre[i] - __popc(St[i]); // runs before word i
   __syncthreads();
-  for (int i = tid; i < nruns; i += HLAB_NT) par[i] = i;
+  for (int i = tid; i < nruns; i += HLAB_NT) par[i] = (uint16_t)i;
   if (MULTI)
     for (int i = tid; i < g.N / 64 + 1; i += HLAB_NT) coin[i] = 0u;
   __syncthreads();
 
   // unions: the row's wrap (at the row's first word), and the two runs over each overlap
   // segment with the next rows along y (and z), segments cut at the word edge
-  volatile int32_t *vpar = par;
+  volatile uint16_t *vpar = par;
   for (int i = tid; i < NBW; i += HLAB_NT) {
     const int r = i / RW, m = i - r * RW;
     const uint32_t w = Q[i];
@@ -786,7 +788,7 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   for (int i = tid; i < nruns; i += HLAB_NT) {
     int x = i;
     for (int p = vpar[x]; p != x; p = vpar[x]) x = p;
-    vpar[i] = x;
+    vpar[i] = (uint16_t)x;
   }
   __syncthreads();
 
@@ -797,7 +799,7 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
     const uint32_t c3 = ((uint32_t)dv.slot[((size_t)s * jb.C + 0) * jb.T + a] << 8) | TAG_HMULTI;
     const uint32_t s_glob = (uint32_t)(jb.s_off + s);
     for (int i = tid; i < nruns; i += HLAB_NT) {
-      if (par[i] != i) continue;
+      if ((int)par[i] != i) continue;
       int lo = 0, hi = NBW - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -833,7 +835,7 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
         const uint32_t pc = __popc(w);
         if (rem < pc) {
           const int r = b / RW, x = 32 * (b - r * RW) + nth_set_bit(w, (int)rem);
-          misc[16] = par[run_of<RW>(St, pre, r, x)];
+          misc[16] = (int)par[run_of<RW>(St, pre, r, x)];
           break;
         }
         rem -= pc;
@@ -857,7 +859,7 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
         const int b = __ffs(seg) - 1;
         seg &= seg - 1u;
         ++id;
-        const int rt = par[id];
+        const int rt = (int)par[id];
         const bool take = MULTI ? ((coin[rt >> 5] >> (rt & 31)) & 1u) != 0u : rt == root0;
         if (take) c |= ((w + (1u << b)) ^ w) & w;
       }
@@ -975,7 +977,7 @@ cudaError_t prepare_houdayer_kernels(int max_smem) {
 
 bool houdayer_labels(const Job &jb) {
   const int RW = (jb.g.L0 + 31) / 32;
-  return label_smem_bytes(jb.g.R * RW, jb.g.N, jb.g.R, jb.g.d) <= HOUD_SMEM_BUDGET;
+  return jb.g.N / 2 <= 65536 && label_smem_bytes(jb.g.R * RW, jb.g.N, jb.g.R, jb.g.d) <= HOUD_SMEM_BUDGET;
 }
 
 // With `scratch` (houdayer_scratch_bytes of the handle's buffer) the split form runs;
@@ -996,7 +998,7 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     const long long pairs = (long long)jb.S * jb.T;
     k_houd_q<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     const int lab = label_smem_bytes(NBW, jb.g.N, jb.g.R, jb.g.d);
-    if (lab <= HOUD_SMEM_BUDGET) {
+    if (houdayer_labels(jb)) {
       pick_label(jb.g.d, RW, multi)<<<(unsigned)pairs, HLAB_NT, (size_t)lab, st>>>(jb, dv, hs);
     } else {
       if (multi) return cudaErrorNotSupported;
