@@ -623,43 +623,16 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_flip(Job jb, Dev dv, HoudSpl
 //
 // A run is a maximal row segment of q = -1 sites, cut at x = 0 (so no run wraps); runs
 // are numbered in canonical order, and the run of site (row r, x) is the number of run
-// starts at or before it minus one.  Unions: the runs at x = 0 and x = L0-1 of a row
+// starts at or before it minus one.  Edges: the runs at x = 0 and x = L0-1 of a row
 // (periodic wrap), and for every pair of neighbouring rows (y+1, and z+1 in 3D) the two
-// runs over each segment where both rows have q = -1.  The forest links the larger root
-// under the smaller with a compare-and-swap, so parents only ever decrease and every
-// walk up a tree ends; finds halve the path they walk.  The work is proportional to the
-// runs, and the CTA's threads share it, so no pair waits on a long serial fill.
+// runs over each segment where both rows have q = -1.  Components come from rounds of
+// hooking and pointer jumping over the edge list (every lane does the same work in a
+// round), which converge in a few rounds on these graphs.  The work is proportional to
+// the runs, and the CTA's threads share it, so no pair waits on a long serial fill.
 // ---------------------------------------------------------------------------------
 constexpr int HLAB_NT = 256;
 
-// Parents are 16-bit run numbers (a pair has at most N/2 <= 65536 runs), which halves the
-// forest's shared memory and lets more CTAs share an SM.
-__device__ __forceinline__ int uf_find(volatile uint16_t *par, int x) {
-  for (;;) {
-    const int p = par[x];
-    if (p == x) return x;
-    const int q = par[p];
-    if (q == p) return p;
-    par[x] = (uint16_t)q; // path halving: q is an ancestor of x
-    x = q;
-  }
-}
-
-__device__ __forceinline__ void uf_union(volatile uint16_t *par, int a, int b) {
-  for (;;) {
-    a = uf_find(par, a);
-    b = uf_find(par, b);
-    if (a == b) return;
-    if (a > b) {
-      const int t = a;
-      a = b;
-      b = t;
-    }
-    const int old = atomicCAS(const_cast<unsigned short *>(par) + b, (unsigned short)b, (unsigned short)a);
-    if (old == b) return;
-    b = old; // b was linked meanwhile: continue from its new parent (smaller than b)
-  }
-}
+// Parents are 16-bit run numbers (a pair has at most N/2 <= 65536 runs).
 
 // Position of the j-th (from 0) set bit of w; w has more than j set bits.
 __device__ __forceinline__ int nth_set_bit(uint32_t w, int j) {
@@ -704,10 +677,16 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *ws, int *total) {
   return ex;
 }
 
+// Edges of a pair's run graph, at most: one wrap per row, and per next row at most 16
+// overlap segments per word.
+__host__ __device__ inline int label_max_edges(int NBW, int R, int D) { return R + 16 * NBW * (D - 1); }
+
 // Shared-memory bytes of the labelling kernel: Q, run starts, run counts per word, scan
-// space, coin bits, 16-bit parents (at most N/2 runs), neighbour rows.
+// space, coin bits, the edges (two 16-bit runs each), 16-bit parents (at most N/2 runs),
+// neighbour rows.
 __host__ __device__ inline int label_smem_bytes(int NBW, int N, int R, int D) {
-  return 4 * (3 * NBW + 32 + (N / 64 + 1)) + ((2 * (N / 2) + 7) & ~7) + ((2 * (D - 1) * R + 7) & ~7);
+  return 4 * (3 * NBW + 32 + (N / 64 + 1)) + 4 * label_max_edges(NBW, R, D) + ((2 * (N / 2) + 7) & ~7) +
+         ((2 * (D - 1) * R + 7) & ~7);
 }
 
 // MULTI: the multi-cluster variant -- every cluster is exchanged by its own coin, the top
@@ -728,7 +707,8 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   int32_t *pre = reinterpret_cast<int32_t *>(St + NBW); // runs before each word
   int32_t *misc = pre + NBW; // [0..8] scan space, [16] seed root, [17] size
   uint32_t *coin = reinterpret_cast<uint32_t *>(misc + 32); // MULTI: coin bit per run
-  uint16_t *par = reinterpret_cast<uint16_t *>(coin + g.N / 64 + 1); // union-find parents, by run
+  ushort2 *edges = reinterpret_cast<ushort2 *>(coin + g.N / 64 + 1); // run graph edges
+  uint16_t *par = reinterpret_cast<uint16_t *>(edges + label_max_edges(NBW, R, D)); // parents, by run
   uint16_t *nrow = par + ((g.N / 2 + 3) & ~3); // [D-1][R] next row along y (and z)
   const uint32_t *Qp = hs.Qg + ((size_t)s * jb.T + a) * NBW;
   uint32_t *Cp = hs.Cg + ((size_t)s * jb.T + a) * NBW;
@@ -741,56 +721,97 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   if (tid == 0) misc[17] = 0;
   __syncthreads();
 
-  // run starts (runs cut at x = 0), counted per word (contiguous chunks of words per thread)
+  // run starts (runs cut at x = 0) and the edges of the run graph, counted per word
+  // (contiguous chunks of words per thread): the row's wrap (at its first word), and one
+  // edge per overlap segment with each next row along y (and z), segments cut at the
+  // word edge
   const int chunk = (NBW + HLAB_NT - 1) / HLAB_NT;
   const int i0 = min(NBW, tid * chunk), i1 = min(NBW, i0 + chunk);
-  int nst = 0;
+  int nst = 0, ned = 0;
   for (int i = i0; i < i1; ++i) {
+    const int r = i / RW, m = i - r * RW;
     const uint32_t w = Q[i];
-    const uint32_t prev = (i % RW) ? (Q[i - 1] >> 31) : 0u;
+    const uint32_t prev = m ? (Q[i - 1] >> 31) : 0u;
     const uint32_t st = w & ~((w << 1) | prev);
     St[i] = st;
     nst += __popc(st);
     pre[i] = nst; // inclusive, within the chunk (made global below)
+    if (m == 0 && (w & 1u) && ((Q[r * RW + ((L0 - 1) >> 5)] >> ((L0 - 1) & 31)) & 1u)) ++ned;
+#pragma unroll
+    for (int t = 0; t < D - 1; ++t) {
+      const uint32_t o = w & Q[nrow[t * R + r] * RW + m];
+      ned += __popc(o & ~(o << 1));
+    }
   }
-  int nruns;
+  int nruns, nedges;
   const int run0 = cta_exclusive_scan(nst, misc, &nruns);
+  const int ed0 = cta_exclusive_scan(ned, misc, &nedges);
   for (int i = i0; i < i1; ++i) pre[i] = run0 + pre[i] - __popc(St[i]); // runs before word i
-  __syncthreads();
   for (int i = tid; i < nruns; i += HLAB_NT) par[i] = (uint16_t)i;
   if (MULTI)
     for (int i = tid; i < g.N / 64 + 1; i += HLAB_NT) coin[i] = 0u;
   __syncthreads();
-
-  // unions: the row's wrap (at the row's first word), and the two runs over each overlap
-  // segment with the next rows along y (and z), segments cut at the word edge
-  volatile uint16_t *vpar = par;
-  for (int i = tid; i < NBW; i += HLAB_NT) {
-    const int r = i / RW, m = i - r * RW;
-    const uint32_t w = Q[i];
-    if (m == 0 && (w & 1u) && ((Q[r * RW + ((L0 - 1) >> 5)] >> ((L0 - 1) & 31)) & 1u))
-      uf_union(vpar, run_of<RW>(St, pre, r, 0), run_of<RW>(St, pre, r, L0 - 1));
+  {
+    int e = ed0;
+    for (int i = i0; i < i1; ++i) {
+      const int r = i / RW, m = i - r * RW;
+      const uint32_t w = Q[i];
+      if (m == 0 && (w & 1u) && ((Q[r * RW + ((L0 - 1) >> 5)] >> ((L0 - 1) & 31)) & 1u))
+        edges[e++] = make_ushort2((unsigned short)run_of<RW>(St, pre, r, 0),
+                                  (unsigned short)run_of<RW>(St, pre, r, L0 - 1));
 #pragma unroll
-    for (int t = 0; t < D - 1; ++t) {
-      const int r2 = nrow[t * R + r];
-      const uint32_t o = w & Q[r2 * RW + m];
-      uint32_t seg = o & ~(o << 1);
-      while (seg) {
-        const int x = 32 * m + __ffs(seg) - 1;
-        seg &= seg - 1u;
-        uf_union(vpar, run_of<RW>(St, pre, r, x), run_of<RW>(St, pre, r2, x));
+      for (int t = 0; t < D - 1; ++t) {
+        const int r2 = nrow[t * R + r];
+        const uint32_t o = w & Q[r2 * RW + m];
+        for (uint32_t sg = o & ~(o << 1); sg; sg &= sg - 1u) {
+          const int x = 32 * m + __ffs(sg) - 1;
+          edges[e++] = make_ushort2((unsigned short)run_of<RW>(St, pre, r, x),
+                                    (unsigned short)run_of<RW>(St, pre, r2, x));
+        }
       }
     }
   }
   __syncthreads();
-  // parents := roots.  The walks only read, and each run's entry is written by its own
-  // thread with its root, so a walk through it meets either value and ends at that root.
-  for (int i = tid; i < nruns; i += HLAB_NT) {
-    int x = i;
-    for (int p = vpar[x]; p != x; p = vpar[x]) x = p;
-    vpar[i] = (uint16_t)x;
+
+  // components: rounds of hooking and pointer jumping.  At the start of a round every
+  // run points at the root of its star; each edge whose ends have different roots hooks
+  // the larger root under the smaller (a compare-and-swap minimum, so parents only
+  // decrease and a root stays the smallest run of its tree); then every run jumps to
+  // its root.  A round without a hook ends the labelling.  Each round merges at least
+  // two trees, so at most nruns rounds are needed (a handful in practice).
+  volatile uint16_t *vpar = par;
+  for (int round = 0; round <= nruns; ++round) {
+    int hooked = 0;
+    for (int e = tid; e < nedges; e += HLAB_NT) {
+      const ushort2 ab = edges[e];
+      const int pa = vpar[ab.x], pb = vpar[ab.y];
+      if (pa != pb) {
+        const int hi = pa > pb ? pa : pb, lo = pa + pb - hi;
+        int cur = vpar[hi];
+        while (lo < cur) {
+          const int old = atomicCAS(const_cast<unsigned short *>(par) + hi, (unsigned short)cur, (unsigned short)lo);
+          if (old == cur) break;
+          cur = old;
+        }
+        hooked = 1;
+      }
+    }
+    if (!__syncthreads_or(hooked)) break;
+    // pointer jumping by doubling (every run to its grandparent, until nothing moves):
+    // log(depth) uniform passes, where walking each run's whole path would cost the
+    // square of a long chain's length
+    for (int it = 0; it <= 16; ++it) {
+      int moved = 0;
+      for (int x = tid; x < nruns; x += HLAB_NT) {
+        const int p = vpar[x], pp = vpar[p];
+        if (pp != p) {
+          vpar[x] = (uint16_t)pp;
+          moved = 1;
+        }
+      }
+      if (!__syncthreads_or(moved)) break;
+    }
   }
-  __syncthreads();
 
   if (MULTI) {
     // a coin for every root run: locate its start (the last word whose run count before
