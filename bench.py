@@ -247,6 +247,50 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
                       "groups in parallel"}
 
 
+def bench_extensions(stream, steps: int = 5):
+    """The rows beyond the core path, each timed with CUDA events on its own stream:
+    the 2D L=128 Houdayer MCS with the single-cluster move and with the multi-cluster
+    variant; one overlap plane-sum measurement of the 3D L=16 job; the 3D L=16 MCS with
+    round-trip counting on and off."""
+    import torch
+
+    from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer, workload_3d_l16
+    from paper_2003_04621_gb300.sgmc import Simulation
+
+    def timed(fn, n):
+        fn(1)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn(n)
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e) / n
+
+    out = {}
+    h = workload_2d_l128_houdayer()
+    for mode, name in ((True, "houdayer_single"), (2, "houdayer_multicluster")):
+        sim = Simulation(2, h.dims, h.n_samples, 2, list(h.temps), houdayer=mode, stream=stream)
+        sim.set_launch(512, 2)
+        ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+        out[name] = {"ms_per_mcs": ms, "attempts_per_ns": h.attempts_per_sweep / (ms * 1e6),
+                     "workload": h.name}
+        sim.close()
+    u = workload_3d_l16()
+    for track in (False, True):
+        sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), track_trips=track, stream=stream)
+        sim.set_launch(256, 2)
+        ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+        out["mcs_trips_on" if track else "mcs_trips_off"] = {"ms_per_mcs": ms,
+                                                             "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6)}
+        if not track:
+            P = torch.empty((u.n_samples, u.T, 3, 16), dtype=torch.int32, device="cuda")
+            qms = timed(lambda n: [sim.qmodes_device(P, stream=stream) for _ in range(n)], steps)
+            out["qmodes_l16"] = {"ms_per_measurement": qms, "pairs": u.n_samples * u.T}
+        sim.close()
+    return out
+
+
 def bench_serving(n_jobs: int, rate: float = 50.0):
     """Poisson(50/s, seed 7) stream of jobs served by continuous batching; p50/p99 latency."""
     import torch
@@ -423,6 +467,7 @@ def main():
     if ws == 1 and not args.no_extras:
         line["batched"] = bench_batched(stream, steps=max(4, args.steps // 8))
         line["serving"] = bench_serving(args.serve_jobs)
+        line["extensions"] = bench_extensions(stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         mcs = 8 if houd else 120  # about 20 s of oracle work on 16 cores
