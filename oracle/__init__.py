@@ -29,6 +29,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sg_oracle.c")
+_SRC_GAUSS = os.path.join(_HERE, "sg_oracle_gauss.c")
 _LIB = os.path.join(_HERE, "libsgoracle.so")
 
 # -ffp-contract=off: no fused multiply-add may change an fp64 result.
@@ -37,9 +38,10 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
 
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/libsgoracle.so`` (plain gcc, no GPU code)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in (_SRC, _SRC_GAUSS))
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, _SRC_GAUSS, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -93,6 +95,26 @@ def _load():
         lib.or_enumerate.restype = ctypes.c_int
         lib.or_enumerate.argtypes = [P, ctypes.c_int, P]
         lib.or_philox4x32_10.argtypes = [P, P, P]
+        # general (fixed-point) couplings, sg_oracle_gauss.c
+        lib.og_create.restype = P
+        lib.og_create.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                  ctypes.c_uint64, P]
+        lib.og_destroy.argtypes = [P]
+        lib.og_sweep.argtypes = [P, ctypes.c_int]
+        lib.og_exchange.argtypes = [P]
+        lib.og_mcs.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        for name in ("og_get_spins", "og_set_spins", "og_get_energies", "og_get_perm", "og_get_counters"):
+            getattr(lib, name).argtypes = [P, P]
+        lib.og_measure.argtypes = [P, P, P]
+        lib.og_check_energies.restype = ctypes.c_int
+        lib.og_check_energies.argtypes = [P]
+        lib.og_enumerate.restype = ctypes.c_int
+        lib.og_enumerate.argtypes = [P, ctypes.c_int, P]
+        lib.og_run_binned.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+        lib.og_exp_f.restype = ctypes.c_float
+        lib.og_exp_f.argtypes = [ctypes.c_float]
+        lib.og_threshold.restype = ctypes.c_uint32
+        lib.og_threshold.argtypes = [ctypes.c_float, ctypes.c_int32]
         _lib = lib
     return _lib
 
@@ -284,3 +306,91 @@ class Oracle:
         if self._lib.or_enumerate(self._h, int(s), _ptr(hist)) != 0:
             raise ValueError("lattice too large to enumerate")
         return hist
+
+
+class OracleGauss:
+    """The general-coupling oracle (sg_oracle_gauss.c): couplings J [S][N][d] as int32
+    fixed point in units of 2^-20, energies int64 in the same units."""
+
+    def __init__(self, ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, temps: Sequence[float],
+                 J_fixed: np.ndarray, sim_seed: int = 1, sample_offset: int = 0):
+        self._lib = _load()
+        self.d = int(ndim)
+        self.dims = tuple(int(x) for x in dims)[: self.d]
+        self.N = int(np.prod(self.dims))
+        self.S, self.C, self.T = int(n_samples), int(n_chains), len(temps)
+        d3 = np.array(list(self.dims) + [1] * (3 - self.d), np.int32)
+        t = np.ascontiguousarray(np.asarray(temps, np.float64))
+        J = np.ascontiguousarray(np.asarray(J_fixed, np.int32).reshape(self.S, self.N, self.d))
+        self._h = self._lib.og_create(self.d, _ptr(d3), self.S, int(sample_offset), self.C, self.T, _ptr(t),
+                                      int(sim_seed), _ptr(J))
+        if not self._h:
+            raise ValueError("og_create failed")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.og_destroy(self._h)
+            self._h = None
+
+    def sweep(self, n: int = 1):
+        self._lib.og_sweep(self._h, int(n))
+
+    def exchange(self):
+        self._lib.og_exchange(self._h)
+
+    def mcs(self, n: int = 1, n_metro: int = 1):
+        self._lib.og_mcs(self._h, int(n), int(n_metro))
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.S, self.C, self.T, self.N), np.uint8)
+        self._lib.og_get_spins(self._h, _ptr(out))
+        return out
+
+    def set_spins(self, bits: np.ndarray):
+        b = np.ascontiguousarray(np.asarray(bits, np.uint8).reshape(self.S, self.C, self.T, self.N))
+        self._lib.og_set_spins(self._h, _ptr(b))
+
+    def energies(self) -> np.ndarray:
+        out = np.zeros((self.S, self.C, self.T), np.int64)
+        self._lib.og_get_energies(self._h, _ptr(out))
+        return out
+
+    def perm(self) -> np.ndarray:
+        out = np.zeros((self.S, self.C, self.T), np.int32)
+        self._lib.og_get_perm(self._h, _ptr(out))
+        return out
+
+    def measure(self):
+        e = np.zeros((self.S, self.C, self.T), np.int64)
+        q = np.zeros((self.S, self.T), np.int32)
+        self._lib.og_measure(self._h, _ptr(e), _ptr(q) if self.C >= 2 else None)
+        return e, (q if self.C >= 2 else None)
+
+    def counters(self) -> dict:
+        c = np.zeros(4, np.uint64)
+        self._lib.og_get_counters(self._h, _ptr(c))
+        return {"t_metro": int(c[0]), "t_pt": int(c[1]), "near_threshold": int(c[2])}
+
+    def check_energies(self) -> int:
+        return int(self._lib.og_check_energies(self._h))
+
+    def enumerate(self, s: int = 0) -> np.ndarray:
+        out = np.zeros(1 << self.N, np.int64)
+        if self._lib.og_enumerate(self._h, int(s), _ptr(out)) != 0:
+            raise ValueError("too many sites to enumerate")
+        return out
+
+    def run_binned(self, n_mcs: int, n_bins: int):
+        sE = np.zeros((self.T, n_bins), np.float64)
+        sE2 = np.zeros((self.T, n_bins), np.float64)
+        self._lib.og_run_binned(self._h, int(n_mcs), int(n_bins), _ptr(sE), _ptr(sE2))
+        return sE, sE2
+
+
+def exp_f(x: float) -> float:
+    """The general-coupling oracle's fp32 exp (Cody-Waite reduction, Taylor to r^6)."""
+    return float(_load().og_exp_f(float(x)))
+
+
+def gauss_threshold(beta_f: float, dE_fixed: int) -> int:
+    return int(_load().og_threshold(float(beta_f), int(dE_fixed)))

@@ -121,3 +121,36 @@ def workload_batched_uneven(seed: int = 1, n_mcs: int = 2000) -> List[Workload]:
                                  sample_offset=base, n_mcs=n_mcs))
             base += count
     return jobs
+
+
+JFIX_SCALE = 1 << 20  # fixed-point couplings: J = J_fixed / 2^20
+
+
+def gaussian_couplings_fixed(n_samples: int, dims: Sequence[int], seed: int = 1, sample_offset: int = 0):
+    """Standard-normal couplings J_ij (Sec. 2.1) for every forward bond, as int32 fixed
+    point in units of 2^-20, [S][N][d] in canonical site order (i = x + L0 (y + L1 z)).
+    Drawn per sample from numpy's PCG64 seeded by (seed, job-wide sample index), so a
+    shard of samples gets the same couplings as inside the whole job; |J| is clipped to
+    8 (a 1e-15 tail)."""
+    import numpy as np
+
+    d = len(dims)
+    N = 1
+    for x in dims:
+        N *= int(x)
+    out = np.empty((n_samples, N, d), np.int32)
+    for s in range(n_samples):
+        rng = np.random.Generator(np.random.PCG64([int(seed), int(sample_offset + s)]))
+        J = np.clip(rng.standard_normal((N, d)), -8.0, 8.0)
+        out[s] = np.rint(J * JFIX_SCALE).astype(np.int32)
+    return out
+
+
+def workload_2d_gauss_l16() -> Workload:
+    """2D Gaussian EA, L=16 (the paper's L=15 sample size made even for the checkerboard),
+    512 samples x 2 chains x 32 temperatures of the phi-family (Eqs. 6-7) in [0.2, 1.5]
+    with phi = 0.406 + 0.014 L (the fit of Eq. 8), int8 spins; couplings from
+    gaussian_couplings_fixed(seed = coupling_seed)."""
+    L = 16
+    return Workload("2d_L16_S512_T32_gauss", 2, (L, L), 512, 2, phi_temps(0.2, 1.5, 32, 0.406 + 0.014 * L),
+                    spin_format="int8", n_mcs=10000)
