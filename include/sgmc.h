@@ -63,6 +63,9 @@ typedef enum {
 } sg_status;
 
 enum { SG_PACKED32 = 0, SG_INT8 = 1 };
+/* Couplings: +-J drawn from coupling_seed (Eq. 2), or general couplings (e.g. Gaussian,
+ * Sec. 2.1) supplied by the caller as fixed point in units of 2^-20 (sg_import_couplings_fixed). */
+enum { SG_COUPLINGS_PM = 0, SG_COUPLINGS_FIXED = 1 };
 
 /* Parameters of one simulation job (Sec. 2; the problem statement of Sec. 2.1-2.4). */
 typedef struct {
@@ -87,6 +90,8 @@ typedef struct {
   int32_t n_metro;       /* Metropolis sweeps per MCS (Sec. 2.4 step 1; usually 1), >= 1  */
   int32_t track_trips;   /* 1: count round trips in temperature after every exchange
                             pass (the tunnelling time of Sec. 2.3; see sg_trips); 0: off */
+  int32_t coupling_kind; /* SG_COUPLINGS_PM or SG_COUPLINGS_FIXED (needs SG_INT8 spins and
+                            houdayer == 0; SG_EUNSUPPORTED otherwise)                     */
 } sg_params;
 
 /* Bytes of device memory a handle with these parameters needs. */
@@ -147,6 +152,20 @@ sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintpt
  * duration in passes (host buffers; synchronises).  SG_EINVAL unless the handle was
  * made with track_trips = 1. */
 sg_status sg_trips(sg_handle *h, uint32_t *n_out, uint64_t *sum_out, uintptr_t stream);
+
+/* General couplings (SG_COUPLINGS_FIXED).  The couplings start at 0; this call sets them
+ * from a host array J[s][i][mu] (int32, canonical site order i = x + L0 (y + L1 z), bond
+ * (i, mu) joining i and i + e_mu), J = J_fixed 2^-20 with |J_fixed| <= 2^23 (else
+ * SG_EINVAL), and recomputes every energy.  The Metropolis rule of these jobs: accept
+ * iff dE <= 0 or r < floor(e 2^32), e an fp32 evaluation of exp(-beta dE) by Cody &
+ * Waite's reduction and a Taylor series to r^6 in single IEEE operations (k_gauss.cu).
+ * Energies of these jobs are int64 in units of 2^-20: sg_measure64 / sg_get_state64
+ * (the int32 calls return SG_EUNSUPPORTED for them). */
+sg_status sg_import_couplings_fixed(sg_handle *h, const int32_t *J_in, uintptr_t stream);
+/* E by temperature slot [S][C][T] (int64, units 2^-20) and N q [S][T]; host buffers, syncs. */
+sg_status sg_measure64(sg_handle *h, int64_t *E_out, int32_t *Q_out, uintptr_t stream);
+/* Energies by replica [S][C][T] (int64, units 2^-20), maps and step counters; syncs. */
+sg_status sg_get_state64(sg_handle *h, int64_t *E_out, int32_t *perm_out, uint64_t *steps_out, uintptr_t stream);
 
 /* Overlap plane sums, the integer part of the Fourier modes of the overlap field behind
  * the spin-glass susceptibility and the correlation length (two-replica measurements,

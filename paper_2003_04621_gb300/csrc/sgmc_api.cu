@@ -16,7 +16,7 @@ namespace {
 
 struct Layout {
   size_t spins, jbits, E, perm, slot, thr, beta, ctr, meas_E, meas_Q, meas_P, gtab, esum, houd, houd_bytes;
-  size_t trip_dir, trip_t0, trip_n, trip_sum, total;
+  size_t trip_dir, trip_t0, trip_n, trip_sum, jfix, E64, meas_E64, jstage, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -43,6 +43,7 @@ struct sg_handle {
   size_t smem;     // its dynamic shared memory
   bool fuse_pt;    // the exchange can run inside the resident kernel
   bool global;     // sweeps stream the lattice from global memory (no resident kernel)
+  bool gauss;      // general fixed-point couplings (k_gauss.cu)
   int n_ctr;       // counters in the device array
 };
 
@@ -69,6 +70,10 @@ sg_status validate(const sg_params *p) {
   if (p->houdayer < 0 || p->houdayer > 2) return SG_EINVAL;
   if (p->houdayer && p->n_chains != 2) return SG_EINVAL;
   if (p->n_metro < 1 || (p->track_trips != 0 && p->track_trips != 1)) return SG_EINVAL;
+  if (p->coupling_kind != SG_COUPLINGS_PM && p->coupling_kind != SG_COUPLINGS_FIXED) return SG_EINVAL;
+  // general couplings: int8 spins (one replica per byte), no cluster move
+  if (p->coupling_kind == SG_COUPLINGS_FIXED && (p->spin_format != SG_INT8 || p->houdayer != 0))
+    return SG_EUNSUPPORTED;
   for (int a = 0; a < p->ndim; ++a)
     if (p->dims[a] % 2) return SG_EUNSUPPORTED; // checkerboard needs even extents
   return SG_OK;
@@ -149,6 +154,12 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   L.trip_t0 = take(tr * S * C * T * 4);
   L.trip_n = take(tr * S * C * 4);
   L.trip_sum = take(tr * S * C * 8);
+  // general couplings: device and staging couplings, int64 energies
+  const size_t gk = p->coupling_kind == SG_COUPLINGS_FIXED ? 1 : 0;
+  L.jfix = take(gk * S * (size_t)g.d * N * 4);
+  L.E64 = take(gk * S * C * T * 8);
+  L.meas_E64 = take(gk * S * C * T * 8);
+  L.jstage = take(gk * S * N * (size_t)g.d * 4);
   L.total = off;
   return L;
 }
@@ -178,6 +189,7 @@ cudaError_t prepare_device() {
   e = prepare_resident_kernels(ms);
   if (e == cudaSuccess) e = prepare_houdayer_kernels(ms);
   if (e == cudaSuccess) e = prepare_state_kernels(ms);
+  if (e == cudaSuccess) e = prepare_gauss_kernels(ms);
   if (e == cudaSuccess && dev < 64) prepared[dev] = true;
   return e;
 }
@@ -235,6 +247,7 @@ sg_status check(sg_handle *h, cudaError_t e) {
 
 template <bool FUSE, bool EONLY>
 sg_status launch_resident(sg_handle *h, cudaStream_t st, int n_mcs, int n_metro) {
+  if (h->gauss) return check(h, sgmc::launch_gauss(h->job, h->dev, FUSE, EONLY, st, n_mcs, n_metro));
   return check(h, sgmc::launch_resident(h->job, h->dev, h->int8fmt != 0, h->nt, h->wpc, FUSE, EONLY, h->smem, st,
                                         n_mcs, n_metro));
 }
@@ -260,7 +273,8 @@ sg_status sweeps(sg_handle *h, int n, cudaStream_t st) {
 }
 
 sg_status exchange(sg_handle *h, cudaStream_t st) {
-  sg_status r = check(h, launch_exchange(h->job, h->dev, st));
+  // general couplings: the energy launch with its exchange fused (int64 energies)
+  sg_status r = h->gauss ? launch_resident<true, true>(h, st, 1, 1) : check(h, launch_exchange(h->job, h->dev, st));
   if (r == SG_OK) h->t_pt += 1;
   return r;
 }
@@ -339,6 +353,13 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
     h->wpc = 1;
     h->smem = 0;
   }
+  if (p->coupling_kind == SG_COUPLINGS_FIXED) {
+    h->smem = gauss_smem_bytes(h->job);
+    if ((int)h->smem > max_dyn_smem()) {
+      delete h;
+      return SG_EUNSUPPORTED;
+    }
+  }
   h->fuse_pt = !h->global && (h->int8fmt ? true : (h->wpc % h->job.Wc == 0));
   h->n_ctr = CTR_PT + T;
 
@@ -362,6 +383,9 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   dv.trip_t0 = tr ? reinterpret_cast<uint32_t *>(h->buf + h->lay.trip_t0) : nullptr;
   dv.trip_n = tr ? reinterpret_cast<uint32_t *>(h->buf + h->lay.trip_n) : nullptr;
   dv.trip_sum = tr ? reinterpret_cast<unsigned long long *>(h->buf + h->lay.trip_sum) : nullptr;
+  h->gauss = p->coupling_kind == SG_COUPLINGS_FIXED;
+  dv.jfix = h->gauss ? reinterpret_cast<int32_t *>(h->buf + h->lay.jfix) : nullptr;
+  dv.E64 = h->gauss ? reinterpret_cast<long long *>(h->buf + h->lay.E64) : nullptr;
 
   cudaStream_t st = as_stream(stream);
   cudaError_t e = prepare_device();
@@ -370,7 +394,8 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->buf + h->lay.beta, h->beta.data(), h->beta.size() * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dv.ctr, 0, (size_t)h->n_ctr * 8, st);
-  if (e == cudaSuccess && tr) e = cudaMemsetAsync(h->buf + h->lay.trip_dir, 0, h->lay.total - h->lay.trip_dir, st);
+  if (e == cudaSuccess && tr) e = cudaMemsetAsync(h->buf + h->lay.trip_dir, 0, h->lay.jfix - h->lay.trip_dir, st);
+  if (e == cudaSuccess && h->gauss) e = cudaMemsetAsync(dv.jfix, 0, h->lay.E64 - h->lay.jfix, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf + h->lay.esum, 0, (size_t)h->job.S * h->job.W * 32 * 4, st);
   if (e == cudaSuccess) e = launch_init(h->job, dv, h->int8fmt != 0, st);
   if (e != cudaSuccess) {
@@ -403,6 +428,7 @@ sg_status sg_exchange(sg_handle *h, uintptr_t stream) {
 }
 
 sg_status sg_houdayer(sg_handle *h, uintptr_t stream) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
   if (h->job.C != 2) return SG_EINVAL;
@@ -419,6 +445,7 @@ bool multi_possible(const sg_handle *h) {
 }
 
 sg_status sg_houdayer_multi(sg_handle *h, uintptr_t stream) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
   if (h->job.C != 2) return SG_EINVAL;
@@ -670,6 +697,7 @@ void sg_batch_destroy(sg_batch *b) { destroy_batch(b); }
 sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
   if (!h || !E_out) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
+  if (h->gauss) return SG_EUNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   return check(h, launch_measure(h->job, h->dev, h->int8fmt != 0, E_out, Q_out, st));
 }
@@ -677,6 +705,7 @@ sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintpt
 sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
   if (!h || !E_out) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
+  if (h->gauss) return SG_EUNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   int32_t *dE = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_E);
   int32_t *dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q);
@@ -723,6 +752,57 @@ sg_status sg_measure_qmodes(sg_handle *h, int32_t *P_out, uintptr_t stream) {
   return poll_device_error(h, st);
 }
 
+sg_status sg_import_couplings_fixed(sg_handle *h, const int32_t *J_in, uintptr_t stream) {
+  if (!h || !J_in) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (!h->gauss) return SG_EINVAL;
+  const size_t n = (size_t)h->job.S * h->job.g.N * h->job.g.d;
+  for (size_t i = 0; i < n; ++i)
+    if (J_in[i] > (1 << 23) || J_in[i] < -(1 << 23)) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  int32_t *stage = reinterpret_cast<int32_t *>(h->buf + h->lay.jstage);
+  cudaError_t e = cudaMemcpyAsync(stage, J_in, n * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_gauss_import(h->job, h->dev, stage, st);
+  if (e != cudaSuccess) return check(h, e);
+  return recompute_energy(h, st);
+}
+
+sg_status sg_measure64(sg_handle *h, int64_t *E_out, int32_t *Q_out, uintptr_t stream) {
+  if (!h || !E_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (!h->gauss) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  long long *dE = reinterpret_cast<long long *>(h->buf + h->lay.meas_E64);
+  int32_t *dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q);
+  const bool want_q = Q_out && h->job.C >= 2;
+  cudaError_t e = launch_gather_energy64(h->job, h->dev, dE, st);
+  if (e == cudaSuccess && want_q) e = launch_measure(h->job, h->dev, true, reinterpret_cast<int32_t *>(
+                                                         h->buf + h->lay.meas_E), dQ, st);
+  const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(E_out, dE, nE * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  return poll_device_error(h, st);
+}
+
+sg_status sg_get_state64(sg_handle *h, int64_t *E_out, int32_t *perm_out, uint64_t *steps_out, uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (!h->gauss) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  const size_t n = (size_t)h->job.S * h->job.C * h->job.T;
+  cudaError_t e = cudaSuccess;
+  if (E_out) e = cudaMemcpyAsync(E_out, h->dev.E64, n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && perm_out) e = cudaMemcpyAsync(perm_out, h->dev.perm, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  if (steps_out) {
+    steps_out[0] = h->t_metro;
+    steps_out[1] = h->t_pt;
+    steps_out[2] = h->t_houd;
+  }
+  return poll_device_error(h, st);
+}
+
 sg_status sg_export_spins(sg_handle *h, uint8_t *spins_out, uintptr_t stream) {
   if (!h || !spins_out) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
@@ -738,12 +818,14 @@ sg_status sg_import_spins(sg_handle *h, const uint8_t *spins_in, uintptr_t strea
 }
 
 sg_status sg_export_couplings(sg_handle *h, int8_t *J_out, uintptr_t stream) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h || !J_out) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
   return check(h, launch_export_couplings(h->job, h->dev, J_out, as_stream(stream)));
 }
 
 sg_status sg_import_couplings(sg_handle *h, const int8_t *J_in, uintptr_t stream) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h || !J_in) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
   cudaStream_t st = as_stream(stream);
@@ -754,6 +836,7 @@ sg_status sg_import_couplings(sg_handle *h, const int8_t *J_in, uintptr_t stream
 sg_status sg_get_state(sg_handle *h, int32_t *E_out, int32_t *perm_out, uint64_t *steps_out, uintptr_t stream) {
   if (!h) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
+  if (h->gauss && E_out) return SG_EUNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   const size_t n = (size_t)h->job.S * h->job.C * h->job.T;
   cudaError_t e = cudaSuccess;
@@ -789,6 +872,7 @@ sg_status sg_counters(sg_handle *h, uint64_t *near_threshold, uint64_t *pt_accep
 }
 
 sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h || !thr_out) return SG_EINVAL;
   const int d = h->job.g.d;
   for (int k = 0; k < h->job.T; ++k)
@@ -797,6 +881,7 @@ sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out) {
 }
 
 sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h) return SG_EINVAL;
   if (h->int8fmt) return (threads == 0 || threads == 256) && (words == 0 || words == 1) ? SG_OK : SG_EUNSUPPORTED;
   if (words == -1) { // stream the lattice from global memory
@@ -825,6 +910,7 @@ sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t 
 }
 
 sg_status sg_sweep_streaming_static(sg_handle *h, int32_t n_sweeps, uintptr_t stream) {
+  if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h || n_sweeps < 0) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
   if (h->int8fmt) return SG_EUNSUPPORTED;

@@ -72,6 +72,9 @@ struct Dev {
   const uint32_t *thr;
   const double *beta;
   unsigned long long *ctr;
+  // general (fixed-point) couplings; null for +-J jobs
+  int32_t *jfix;  // [S][d][N] colour-split site order, units of 2^-20
+  long long *E64; // [S][C][T] energies by replica, units of 2^-20
   // round trips in temperature (null when the job does not track them)
   int32_t *trip_dir;             // [S][C][T] 0: no extreme yet, 1: lowest slot last, 2: highest last
   uint32_t *trip_t0;             // [S][C][T] exchange pass of the trip's arrival at the lowest slot
@@ -406,4 +409,11 @@ cudaError_t launch_measure(const Job &jb, const Dev &dv, bool int8fmt, int32_t *
 int qmodes_lmax(const Job &jb);
 cudaError_t launch_qmodes(const Job &jb, const Dev &dv, bool int8fmt, int32_t *P_out, cudaStream_t st);
 cudaError_t prepare_state_kernels(int max_smem);
+// General couplings (k_gauss.cu).
+size_t gauss_smem_bytes(const Job &jb);
+cudaError_t launch_gauss(const Job &jb, const Dev &dv, bool fuse_pt, bool energy_only, cudaStream_t st, int n_mcs,
+                         int n_metro);
+cudaError_t launch_gauss_import(const Job &jb, const Dev &dv, const int32_t *stage, cudaStream_t st);
+cudaError_t launch_gather_energy64(const Job &jb, const Dev &dv, long long *E_out, cudaStream_t st);
+cudaError_t prepare_gauss_kernels(int max_smem);
 } // namespace sgmc

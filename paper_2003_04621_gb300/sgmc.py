@@ -45,12 +45,14 @@ class Params(ctypes.Structure):
         ("houdayer", ctypes.c_int32),
         ("n_metro", ctypes.c_int32),
         ("track_trips", ctypes.c_int32),
+        ("coupling_kind", ctypes.c_int32),
     ]
 
 
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
-    "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
+    "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
@@ -87,6 +89,9 @@ def lib():
         "sg_export_couplings": [P, P, U],
         "sg_import_couplings": [P, P, U],
         "sg_get_state": [P, P, P, P, U],
+        "sg_import_couplings_fixed": [P, P, U],
+        "sg_measure64": [P, P, P, U],
+        "sg_get_state64": [P, P, P, P, U],
         "sg_counters": [P, P, P, P, U],
         "sg_thresholds": [P, P],
         "sg_set_launch": [P, I32, I32],
@@ -116,7 +121,8 @@ def _check(status: int, where: str):
 
 def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, temps: Sequence[float],
                 coupling_seed: int = 1, sim_seed: int = 1, p_plus: float = 0.5, spin_format: str = "packed",
-                houdayer=False, n_metro: int = 1, sample_offset: int = 0, track_trips: bool = False):
+                houdayer=False, n_metro: int = 1, sample_offset: int = 0, track_trips: bool = False,
+                couplings: str = "pm"):
     """Fill an sg_params; returns (params, temps_array) -- keep the array alive."""
     t = np.ascontiguousarray(np.asarray(temps, dtype=np.float64))
     p = Params()
@@ -135,6 +141,9 @@ def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, t
     p.houdayer = 2 if (houdayer is not True and houdayer == 2) else int(bool(houdayer))
     p.n_metro = int(n_metro)
     p.track_trips = int(bool(track_trips))
+    if couplings not in ("pm", "fixed"):
+        raise ValueError("couplings must be 'pm' (+-J from coupling_seed) or 'fixed' (set_couplings_fixed)")
+    p.coupling_kind = 0 if couplings == "pm" else 1
     return p, t
 
 
@@ -157,7 +166,7 @@ class Simulation:
 
     def __init__(self, ndim, dims, n_samples, n_chains, temps, coupling_seed=1, sim_seed=1, p_plus=0.5,
                  spin_format="packed", houdayer=False, n_metro=1, sample_offset=0, stream=None, device=None,
-                 device_buffer=None, track_trips=False):
+                 device_buffer=None, track_trips=False, couplings="pm"):
         """device_buffer: optional (device pointer, bytes) the job lives in (256-byte
         aligned, at least query_bytes); by default a torch buffer is allocated."""
         import torch
@@ -171,7 +180,8 @@ class Simulation:
         self.S, self.C, self.T = int(n_samples), int(n_chains), len(temps)
         self.params, self._temps = make_params(ndim, dims, n_samples, n_chains, temps, coupling_seed, sim_seed,
                                                p_plus, spin_format, houdayer, n_metro, sample_offset,
-                                               track_trips)
+                                               track_trips, couplings)
+        self.gauss = couplings == "fixed"
         self.bytes = query_bytes(self.params)
         if device_buffer is not None:
             self._buf = None
@@ -227,10 +237,19 @@ class Simulation:
         _check(lib().sg_sweep_streaming_static(self._h, int(n), self._s(stream)), "sg_sweep_streaming_static")
 
     # -- observables and state --------------------------------------------------------
+    def _measure64(self, stream=None):
+        E = np.zeros((self.S, self.C, self.T), np.int64)
+        Q = np.zeros((self.S, self.T), np.int32) if self.C >= 2 else None
+        _check(lib().sg_measure64(self._h, E.ctypes.data, Q.ctypes.data if Q is not None else None,
+                                  self._s(stream)), "sg_measure64")
+        return E, Q
+
     def measure(self, stream=None, out=None):
         """(E by slot [S][C][T], N q [S][T] or None) as numpy arrays; synchronises.
         `out` = (E, Q) writes into given C-contiguous int32 arrays instead (e.g. numpy
         views of pinned host tensors, so that the device-to-host copies are direct)."""
+        if self.gauss:
+            return self._measure64(stream)
         if out is None:
             E = np.zeros((self.S, self.C, self.T), np.int32)
             Q = np.zeros((self.S, self.T), np.int32) if self.C >= 2 else None
@@ -304,13 +323,25 @@ class Simulation:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
 
     def state(self, stream=None):
-        """(E by replica [S][C][T], perm [S][C][T], steps (t_metro, t_pt, t_houd))."""
-        E = np.zeros((self.S, self.C, self.T), np.int32)
+        """(E by replica [S][C][T], perm [S][C][T], steps (t_metro, t_pt, t_houd)).  E is
+        int32 for +-J jobs, int64 in units of 2^-20 for general couplings."""
         perm = np.zeros((self.S, self.C, self.T), np.int32)
         steps = np.zeros(3, np.uint64)
-        _check(lib().sg_get_state(self._h, E.ctypes.data, perm.ctypes.data, steps.ctypes.data, self._s(stream)),
-               "sg_get_state")
+        if self.gauss:
+            E = np.zeros((self.S, self.C, self.T), np.int64)
+            _check(lib().sg_get_state64(self._h, E.ctypes.data, perm.ctypes.data, steps.ctypes.data,
+                                        self._s(stream)), "sg_get_state64")
+        else:
+            E = np.zeros((self.S, self.C, self.T), np.int32)
+            _check(lib().sg_get_state(self._h, E.ctypes.data, perm.ctypes.data, steps.ctypes.data,
+                                      self._s(stream)), "sg_get_state")
         return E, perm, tuple(int(x) for x in steps)
+
+    def set_couplings_fixed(self, J_fixed, stream=None):
+        """General couplings: int32 [S][N][d] in units of 2^-20 (canonical site order);
+        recomputes the energies."""
+        J = np.ascontiguousarray(np.asarray(J_fixed, np.int32).reshape(self.S, self.N, self.ndim))
+        _check(lib().sg_import_couplings_fixed(self._h, J.ctypes.data, self._s(stream)), "sg_import_couplings_fixed")
 
     def counters(self, stream=None) -> dict:
         near = np.zeros(1, np.uint64)
