@@ -250,8 +250,8 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
 def bench_extensions(stream, steps: int = 5):
     """The rows beyond the core path, each timed with CUDA events on its own stream:
     the 2D L=128 Houdayer MCS with the single-cluster move and with the multi-cluster
-    variant; one overlap plane-sum measurement of the 3D L=16 job; the 3D L=16 MCS with
-    round-trip counting on and off."""
+    variant; the 2D L=16 Gaussian-coupling MCS; one overlap plane-sum measurement of the
+    3D L=16 job; the 3D L=16 MCS with round-trip counting on and off."""
     import torch
 
     from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer, workload_3d_l16
@@ -276,6 +276,17 @@ def bench_extensions(stream, steps: int = 5):
         out[name] = {"ms_per_mcs": ms, "attempts_per_ns": h.attempts_per_sweep / (ms * 1e6),
                      "workload": h.name}
         sim.close()
+    # the 2D Gaussian job (general couplings, int8 spins, fixed-point energies)
+    from paper_2003_04621_gb300.inputs import gaussian_couplings_fixed, workload_2d_gauss_l16
+
+    gw = workload_2d_gauss_l16()
+    sim = Simulation(2, gw.dims, gw.n_samples, 2, list(gw.temps), spin_format="int8", couplings="fixed",
+                     stream=stream)
+    sim.set_couplings_fixed(gaussian_couplings_fixed(gw.n_samples, gw.dims, seed=gw.coupling_seed), stream=stream)
+    ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+    out["gauss_2d_l16"] = {"ms_per_mcs": ms, "attempts_per_ns": gw.attempts_per_sweep / (ms * 1e6),
+                           "workload": gw.name}
+    sim.close()
     u = workload_3d_l16()
     for track in (False, True):
         sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), track_trips=track, stream=stream)
