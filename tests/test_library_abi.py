@@ -55,9 +55,22 @@ def test_parameter_validation_needs_no_gpu(libsgmc):
         (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[-1.0, 1.0]), 1),
         (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=1, temps=[1.0], houdayer=True), 1),
         (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0], p_plus=1.5), 1),
+        (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0 + k for k in range(4097)]), 1),  # > 4096
+        (dict(ndim=3, dims=(512, 512, 512), n_samples=1, n_chains=2, temps=[1.0]), 5),  # > 2^26 sites
+        (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0], couplings="fixed"), 5),  # packed
+        (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0], couplings="fixed", spin_format="int8",
+              houdayer=True), 5),
     ]
     for kw, want in cases:
         p, _t = sgmc.make_params(**kw)
         with pytest.raises(sgmc.SGError) as e:
             sgmc.query_bytes(p)
         assert e.value.status == want, kw
+    # raw fields outside their ranges
+    for field, value in (("houdayer", 3), ("track_trips", 2), ("coupling_kind", 2), ("spin_format", 7),
+                         ("n_metro", 0)):
+        p, _t = sgmc.make_params(2, (4, 4), 1, 2, [1.0])
+        setattr(p, field, value)
+        with pytest.raises(sgmc.SGError) as e:
+            sgmc.query_bytes(p)
+        assert e.value.status == 1, field
