@@ -681,11 +681,18 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *ws, int *total) {
 // overlap segments per word.
 __host__ __device__ inline int label_max_edges(int NBW, int R, int D) { return R + 16 * NBW * (D - 1); }
 
+// Edges kept in shared memory: up to N/4 + R (a random q field with half its sites at
+// -1 has about N/7); a pair with more recomputes its edges from the bitmaps every round.
+__host__ __device__ inline int label_edge_cap(int NBW, int N, int R, int D) {
+  const int m = label_max_edges(NBW, R, D), c = N / 4 + R;
+  return m < c ? m : c;
+}
+
 // Shared-memory bytes of the labelling kernel: Q, run starts, run counts per word, scan
 // space, coin bits, the edges (two 16-bit runs each), 16-bit parents (at most N/2 runs),
 // neighbour rows.
 __host__ __device__ inline int label_smem_bytes(int NBW, int N, int R, int D) {
-  return 4 * (3 * NBW + 32 + (N / 64 + 1)) + 4 * label_max_edges(NBW, R, D) + ((2 * (N / 2) + 7) & ~7) +
+  return 4 * (3 * NBW + 32 + (N / 64 + 1)) + 4 * label_edge_cap(NBW, N, R, D) + ((2 * (N / 2) + 7) & ~7) +
          ((2 * (D - 1) * R + 7) & ~7);
 }
 
@@ -708,7 +715,8 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   int32_t *misc = pre + NBW; // [0..8] scan space, [16] seed root, [17] size
   uint32_t *coin = reinterpret_cast<uint32_t *>(misc + 32); // MULTI: coin bit per run
   ushort2 *edges = reinterpret_cast<ushort2 *>(coin + g.N / 64 + 1); // run graph edges
-  uint16_t *par = reinterpret_cast<uint16_t *>(edges + label_max_edges(NBW, R, D)); // parents, by run
+  const int ecap = label_edge_cap(NBW, g.N, R, D);
+  uint16_t *par = reinterpret_cast<uint16_t *>(edges + ecap); // parents, by run
   uint16_t *nrow = par + ((g.N / 2 + 3) & ~3); // [D-1][R] next row along y (and z)
   const uint32_t *Qp = hs.Qg + ((size_t)s * jb.T + a) * NBW;
   uint32_t *Cp = hs.Cg + ((size_t)s * jb.T + a) * NBW;
@@ -751,7 +759,8 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   if (MULTI)
     for (int i = tid; i < g.N / 64 + 1; i += HLAB_NT) coin[i] = 0u;
   __syncthreads();
-  {
+  const bool stored = nedges <= ecap; // the same on every thread
+  if (stored) {
     int e = ed0;
     for (int i = i0; i < i1; ++i) {
       const int r = i / RW, m = i - r * RW;
@@ -780,20 +789,41 @@ __global__ void __launch_bounds__(HLAB_NT) k_houd_label(Job jb, Dev dv, HoudSpli
   // its root.  A round without a hook ends the labelling.  Each round merges at least
   // two trees, so at most nruns rounds are needed (a handful in practice).
   volatile uint16_t *vpar = par;
+  auto hook = [&](int a_run, int b_run, int &hooked) {
+    const int pa = vpar[a_run], pb = vpar[b_run];
+    if (pa != pb) {
+      const int hi = pa > pb ? pa : pb, lo = pa + pb - hi;
+      int cur = vpar[hi];
+      while (lo < cur) {
+        const int old = atomicCAS(const_cast<unsigned short *>(par) + hi, (unsigned short)cur, (unsigned short)lo);
+        if (old == cur) break;
+        cur = old;
+      }
+      hooked = 1;
+    }
+  };
   for (int round = 0; round <= nruns; ++round) {
     int hooked = 0;
-    for (int e = tid; e < nedges; e += HLAB_NT) {
-      const ushort2 ab = edges[e];
-      const int pa = vpar[ab.x], pb = vpar[ab.y];
-      if (pa != pb) {
-        const int hi = pa > pb ? pa : pb, lo = pa + pb - hi;
-        int cur = vpar[hi];
-        while (lo < cur) {
-          const int old = atomicCAS(const_cast<unsigned short *>(par) + hi, (unsigned short)cur, (unsigned short)lo);
-          if (old == cur) break;
-          cur = old;
+    if (stored) {
+      for (int e = tid; e < nedges; e += HLAB_NT) {
+        const ushort2 ab = edges[e];
+        hook(ab.x, ab.y, hooked);
+      }
+    } else {
+      for (int i = i0; i < i1; ++i) {
+        const int r = i / RW, m = i - r * RW;
+        const uint32_t w = Q[i];
+        if (m == 0 && (w & 1u) && ((Q[r * RW + ((L0 - 1) >> 5)] >> ((L0 - 1) & 31)) & 1u))
+          hook(run_of<RW>(St, pre, r, 0), run_of<RW>(St, pre, r, L0 - 1), hooked);
+#pragma unroll
+        for (int t = 0; t < D - 1; ++t) {
+          const int r2 = nrow[t * R + r];
+          const uint32_t o = w & Q[r2 * RW + m];
+          for (uint32_t sg = o & ~(o << 1); sg; sg &= sg - 1u) {
+            const int x = 32 * m + __ffs(sg) - 1;
+            hook(run_of<RW>(St, pre, r, x), run_of<RW>(St, pre, r2, x), hooked);
+          }
         }
-        hooked = 1;
       }
     }
     if (!__syncthreads_or(hooked)) break;

@@ -169,3 +169,40 @@ def test_multicluster_refused_without_scratch():
     with pytest.raises(SGError) as e:  # labels beyond one CTA's shared memory
         big.houdayer_multi()
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_houdayer_striped_q_field(oracle_mod, multi):
+    """Chains planted to differ on every odd column: N/2 q = -1 sites in L0/2 rings, with
+    more run-graph edges than the labelling keeps in shared memory, so the labels are
+    built from edges recomputed every round."""
+    kw = dict(ndim=2, dims=(32, 16), n_samples=2, n_chains=2, temps=geometric_temps(0.4, 1.5, 4), sim_seed=9,
+              houdayer=2 if multi else True)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    bits = orc.spins()
+    x = np.arange(32 * 16) % 32
+    stripe = (x & 1).astype(np.uint8)
+    perm = orc.perm()[0]
+    for s in range(2):
+        for k in range(4):
+            a, b = perm[s, 0, k], perm[s, 1, k]
+            bits[s, 1, b] = bits[s, 0, a] ^ stripe
+    orc.set_spins(bits)
+    sim.set_spins(bits)
+    assert_same_state(sim, orc, "planted")
+    op = "H" if multi else "h"
+    run_pair_from(sim, orc, [op, op, "x", op])
+
+
+def run_pair_from(sim, orc, ops):
+    for t, op in enumerate(ops):
+        if op == "h":
+            sim.houdayer()
+            orc.houdayer()
+        elif op == "H":
+            sim.houdayer_multi()
+            orc.houdayer_multi()
+        elif op == "x":
+            sim.exchange()
+            orc.exchange()
+        assert_same_state(sim, orc, f"step {t} ({op})")
