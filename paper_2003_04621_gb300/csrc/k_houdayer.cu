@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_q(Job jb, Dev dv, HoudSplit 
   uint32_t *Qb = hs.Qg + (size_t)s * T * NBW;
   const uint32_t tmask = T >= 32 ? FULLM : ((1u << T) - 1u);
   uint32_t mpart = 0u;
-  for (int tb = 0; tb < NBW; tb += HQ_TB) {
+  for (int tb = blockIdx.y * HQ_TB; tb < NBW; tb += gridDim.y * HQ_TB) {
     const int nb = min(HQ_TB, NBW - tb);
     // HQ_U blocks per warp at a time: their words are loaded before any is used
     for (int j0 = warp; j0 < nb; j0 += nwarps * HQ_U) {
@@ -499,7 +499,8 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_q(Job jb, Dev dv, HoudSplit 
   }
   if (lane < T && mpart) atomicAdd(&Mc[lane], mpart);
   __syncthreads();
-  if (tid < 32) hs.Mg[(size_t)s * 32 + tid] = Mc[tid];
+  // the sample's CTAs (blockIdx.y = part of its blocks) add into M, cleared before launch
+  if (tid < 32 && Mc[tid]) atomicAdd(&hs.Mg[(size_t)s * 32 + tid], Mc[tid]);
 }
 
 template <int D, int RW, bool SMEM>
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_flip(Job jb, Dev dv, HoudSpl
   uint32_t *w0w = dv.spins + ((size_t)s * jb.W + 0) * jb.g.N;
   uint32_t *w1w = dv.spins + ((size_t)s * jb.W + 1) * jb.g.N;
   const uint32_t *Cb = hs.Cg + (size_t)s * T * NBW;
-  for (int tb = 0; tb < NBW; tb += HQ_TB) {
+  for (int tb = blockIdx.y * HQ_TB; tb < NBW; tb += gridDim.y * HQ_TB) {
     const int nb = min(HQ_TB, NBW - tb);
     for (int e = tid; e < T * nb; e += HSPLIT_NT) {
       const int a = e / nb, j = e - a * nb;
@@ -1047,7 +1048,17 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     int smem = 0;
     fill_shape(jb, NBW, &hs.wpb, &hs.in_smem, &smem);
     const long long pairs = (long long)jb.S * jb.T;
-    k_houd_q<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    // per-sample kernels: about four CTAs per SM (parts of a sample's blocks)
+    int dev = 0, n_sm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    int parts = (4 * n_sm + jb.S - 1) / jb.S;
+    const int tiles = (NBW + HQ_TB - 1) / HQ_TB;
+    parts = parts < 1 ? 1 : (parts > 8 ? 8 : parts);
+    parts = parts > tiles ? tiles : parts;
+    const dim3 pgrid((unsigned)jb.S, (unsigned)parts);
+    cudaError_t e0 = cudaMemsetAsync(hs.Mg, 0, (size_t)jb.S * 32 * 4, st);
+    if (e0 != cudaSuccess) return e0;
+    k_houd_q<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     const int lab = label_smem_bytes(NBW, jb.g.N, jb.g.R, jb.g.d);
     if (houdayer_labels(jb)) {
       pick_label(jb.g.d, RW, multi)<<<(unsigned)pairs, HLAB_NT, (size_t)lab, st>>>(jb, dv, hs);
@@ -1057,7 +1068,7 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
       pick_fill(jb.g.d, RW, hs.in_smem != 0)<<<(unsigned)((pairs + hs.wpb - 1) / hs.wpb), 32 * hs.wpb,
                                                 (size_t)smem, st>>>(jb, dv, hs);
     }
-    k_houd_flip<<<(unsigned)jb.S, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    k_houd_flip<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     return cudaGetLastError();
   }
   if (multi) return cudaErrorNotSupported; // the multi-cluster variant labels in the split form only
