@@ -253,6 +253,16 @@ void sg_batch_destroy(sg_batch *b);
 sg_status sg_sweep_streaming_static(sg_handle *h, int32_t n_sweeps, uintptr_t stream);
 
 /* Free the host-side handle.  The caller frees the device buffer afterwards. */
+/* Checkpoint and resume (long runs): a checkpoint is a host blob of
+ * sg_checkpoint_bytes bytes holding the parameters that fix the layout and the
+ * dynamics, the temperatures, the step counters and the handle's whole device buffer.
+ * sg_checkpoint writes it (synchronises the stream); sg_restore loads it into a handle
+ * made with the same parameters (else SG_EINVAL), after which the job continues exactly
+ * as the checkpointed one would have. */
+sg_status sg_checkpoint_bytes(sg_handle *h, size_t *bytes);
+sg_status sg_checkpoint(sg_handle *h, void *host_out, size_t bytes, uintptr_t stream);
+sg_status sg_restore(sg_handle *h, const void *host_in, size_t bytes, uintptr_t stream);
+
 void sg_destroy(sg_handle *h);
 
 /* Static description of a status code. */

@@ -931,6 +931,97 @@ sg_status sg_sweep_streaming_static(sg_handle *h, int32_t n_sweeps, uintptr_t st
   return r;
 }
 
+// Checkpoints: a fixed header (the parameters that fix the buffer's layout and the
+// dynamics, and the host step counters), the temperatures, then the handle's whole
+// device buffer.  The engine's state lives entirely in that buffer and those counters.
+namespace {
+struct CkptHeader {
+  uint64_t magic;
+  uint32_t version, reserved;
+  int32_t ndim, dims[3], n_samples, sample_offset, n_chains, n_temps, spin_format, houdayer, n_metro, track_trips,
+      coupling_kind, pad;
+  uint64_t sim_seed, coupling_seed;
+  double p_plus;
+  uint64_t t_metro, t_pt, t_houd, device_bytes;
+};
+constexpr uint64_t CKPT_MAGIC = 0x31544B5043474D53ull; // "SMGCPKT1"
+
+CkptHeader header_of(const sg_handle *h) {
+  CkptHeader c;
+  memset(&c, 0, sizeof(c));
+  c.magic = CKPT_MAGIC;
+  c.version = 1;
+  c.ndim = h->p.ndim;
+  for (int a = 0; a < 3; ++a) c.dims[a] = a < h->p.ndim ? h->p.dims[a] : 1;
+  c.n_samples = h->p.n_samples;
+  c.sample_offset = h->p.sample_offset;
+  c.n_chains = h->p.n_chains;
+  c.n_temps = h->p.n_temps;
+  c.spin_format = h->p.spin_format;
+  c.houdayer = h->p.houdayer;
+  c.n_metro = h->p.n_metro;
+  c.track_trips = h->p.track_trips;
+  c.coupling_kind = h->p.coupling_kind;
+  c.sim_seed = h->p.sim_seed;
+  c.coupling_seed = h->p.coupling_seed;
+  c.p_plus = h->p.p_plus;
+  c.t_metro = h->t_metro;
+  c.t_pt = h->t_pt;
+  c.t_houd = h->t_houd;
+  c.device_bytes = h->lay.total;
+  return c;
+}
+
+size_t ckpt_bytes(const sg_handle *h) {
+  return sizeof(CkptHeader) + sizeof(double) * (size_t)h->p.n_temps + h->lay.total;
+}
+} // namespace
+
+sg_status sg_checkpoint_bytes(sg_handle *h, size_t *bytes) {
+  if (!h || !bytes) return SG_EINVAL;
+  *bytes = ckpt_bytes(h);
+  return SG_OK;
+}
+
+sg_status sg_checkpoint(sg_handle *h, void *host_out, size_t bytes, uintptr_t stream) {
+  if (!h || !host_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (bytes < ckpt_bytes(h)) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  const CkptHeader c = header_of(h);
+  char *out = static_cast<char *>(host_out);
+  memcpy(out, &c, sizeof(c));
+  memcpy(out + sizeof(c), h->temps.data(), sizeof(double) * (size_t)h->p.n_temps);
+  const cudaError_t e = cudaMemcpyAsync(out + sizeof(c) + sizeof(double) * (size_t)h->p.n_temps, h->buf,
+                                        h->lay.total, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return check(h, e);
+  return poll_device_error(h, st);
+}
+
+sg_status sg_restore(sg_handle *h, const void *host_in, size_t bytes, uintptr_t stream) {
+  if (!h || !host_in) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (bytes < ckpt_bytes(h)) return SG_EINVAL;
+  const char *in = static_cast<const char *>(host_in);
+  CkptHeader c, mine = header_of(h);
+  memcpy(&c, in, sizeof(c));
+  // everything but the step counters must match this handle
+  mine.t_metro = c.t_metro;
+  mine.t_pt = c.t_pt;
+  mine.t_houd = c.t_houd;
+  if (memcmp(&c, &mine, sizeof(c)) != 0) return SG_EINVAL;
+  if (memcmp(in + sizeof(c), h->temps.data(), sizeof(double) * (size_t)h->p.n_temps) != 0) return SG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(h->buf, in + sizeof(c) + sizeof(double) * (size_t)h->p.n_temps, h->lay.total,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return check(h, e);
+  h->t_metro = c.t_metro;
+  h->t_pt = c.t_pt;
+  h->t_houd = c.t_houd;
+  return SG_OK;
+}
+
 void sg_destroy(sg_handle *h) { delete h; }
 
 const char *sg_strerror(sg_status s) {

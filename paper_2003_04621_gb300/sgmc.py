@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
     "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
-    "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_checkpoint_bytes", "sg_checkpoint",
+    "sg_restore", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
@@ -92,6 +93,9 @@ def lib():
         "sg_import_couplings_fixed": [P, P, U],
         "sg_measure64": [P, P, P, U],
         "sg_get_state64": [P, P, P, P, U],
+        "sg_checkpoint_bytes": [P, ctypes.POINTER(SZ)],
+        "sg_checkpoint": [P, P, SZ, U],
+        "sg_restore": [P, P, SZ, U],
         "sg_counters": [P, P, P, P, U],
         "sg_thresholds": [P, P],
         "sg_set_launch": [P, I32, I32],
@@ -336,6 +340,19 @@ class Simulation:
             _check(lib().sg_get_state(self._h, E.ctypes.data, perm.ctypes.data, steps.ctypes.data,
                                       self._s(stream)), "sg_get_state")
         return E, perm, tuple(int(x) for x in steps)
+
+    def checkpoint(self, stream=None) -> np.ndarray:
+        """The job's whole state as a host byte array (see sg_checkpoint)."""
+        n = ctypes.c_size_t()
+        _check(lib().sg_checkpoint_bytes(self._h, ctypes.byref(n)), "sg_checkpoint_bytes")
+        blob = np.empty(n.value, np.uint8)
+        _check(lib().sg_checkpoint(self._h, blob.ctypes.data, n.value, self._s(stream)), "sg_checkpoint")
+        return blob
+
+    def restore(self, blob: np.ndarray, stream=None):
+        """Resume from a checkpoint of a job with the same parameters."""
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().sg_restore(self._h, b.ctypes.data, b.size, self._s(stream)), "sg_restore")
 
     def set_couplings_fixed(self, J_fixed, stream=None):
         """General couplings: int32 [S][N][d] in units of 2^-20 (canonical site order);
