@@ -263,6 +263,13 @@ sg_status sg_checkpoint_bytes(sg_handle *h, size_t *bytes);
 sg_status sg_checkpoint(sg_handle *h, void *host_out, size_t bytes, uintptr_t stream);
 sg_status sg_restore(sg_handle *h, const void *host_in, size_t bytes, uintptr_t stream);
 
+/* Failure-detection self-test: a kernel waits (at most max_tries polls, 1..2^20) on an
+ * mbarrier that nothing completes, as the kernels' waits on their bulk copies are
+ * bounded.  The wait runs out, the kernel records the error and returns, and the call
+ * reports SG_ETIMEOUT; the handle is then poisoned (every later call returns
+ * SG_ETIMEOUT), exactly as after a copy that never landed.  No fault, trap or hang. */
+sg_status sg_selftest_wait(sg_handle *h, int32_t max_tries, uintptr_t stream);
+
 void sg_destroy(sg_handle *h);
 
 /* Static description of a status code. */

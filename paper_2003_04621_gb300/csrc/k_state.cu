@@ -1,6 +1,7 @@
 // k_state.cu -- creation (Eq. 2 couplings, hot start), import/export of spins and
 // couplings in plain layouts, and the measurement of E by slot and N q (Eqs. 3-4).
 #include "sgmc_internal.cuh"
+#include "sgmc_tma.cuh"
 
 namespace sgmc {
 
@@ -400,6 +401,21 @@ cudaError_t prepare_state_kernels(int max_smem) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Failure detection without a fault: one thread waits, bounded, on an mbarrier that no
+// arrival or copy will ever complete; when the bound runs out it records the same error
+// flag a lost TMA copy would, and returns.  The host then reads SG_ETIMEOUT.
+__global__ void k_wait_selftest(unsigned long long *ctr, uint32_t max_tries) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, max_tries)) atomicOr(&ctr[CTR_ERROR], ERR_TMA_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(const Dev &dv, uint32_t max_tries, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(dv.ctr, max_tries);
+  return cudaGetLastError();
 }
 
 namespace {

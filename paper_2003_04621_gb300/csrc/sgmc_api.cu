@@ -1022,6 +1022,14 @@ sg_status sg_restore(sg_handle *h, const void *host_in, size_t bytes, uintptr_t 
   return SG_OK;
 }
 
+sg_status sg_selftest_wait(sg_handle *h, int32_t max_tries, uintptr_t stream) {
+  if (!h || max_tries < 1 || max_tries > (1 << 20)) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  const sg_status r = check(h, launch_wait_selftest(h->dev, (uint32_t)max_tries, st));
+  return r == SG_OK ? poll_device_error(h, st) : r;
+}
+
 void sg_destroy(sg_handle *h) { delete h; }
 
 const char *sg_strerror(sg_status s) {

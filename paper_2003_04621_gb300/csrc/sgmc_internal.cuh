@@ -409,6 +409,8 @@ cudaError_t launch_measure(const Job &jb, const Dev &dv, bool int8fmt, int32_t *
 int qmodes_lmax(const Job &jb);
 cudaError_t launch_qmodes(const Job &jb, const Dev &dv, bool int8fmt, int32_t *P_out, cudaStream_t st);
 cudaError_t prepare_state_kernels(int max_smem);
+// A bounded wait that runs out by design (failure detection self-test).
+cudaError_t launch_wait_selftest(const Dev &dv, uint32_t max_tries, cudaStream_t st);
 // General couplings (k_gauss.cu).
 size_t gauss_smem_bytes(const Job &jb);
 cudaError_t launch_gauss(const Job &jb, const Dev &dv, bool fuse_pt, bool energy_only, cudaStream_t st, int n_mcs,

@@ -53,7 +53,7 @@ EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
     "sg_measure", "sg_measure_device", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
     "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_checkpoint_bytes", "sg_checkpoint",
-    "sg_restore", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
+    "sg_restore", "sg_selftest_wait", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
 )
@@ -96,6 +96,7 @@ def lib():
         "sg_checkpoint_bytes": [P, ctypes.POINTER(SZ)],
         "sg_checkpoint": [P, P, SZ, U],
         "sg_restore": [P, P, SZ, U],
+        "sg_selftest_wait": [P, I32, U],
         "sg_counters": [P, P, P, P, U],
         "sg_thresholds": [P, P],
         "sg_set_launch": [P, I32, I32],
