@@ -56,22 +56,24 @@ static uint32_t og_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, ui
 float og_exp_f(float x) {
   volatile float vx = x; /* keep the compiler from reassociating anything below */
   float xv = vx;
-  const float inv_ln2 = 1.44269502162933349609375f;
-  const float ln2_hi = 0.693145751953125f;
-  const float ln2_lo = 1.428606765330187045037746429443359375e-06f;
+  /* 1/ln 2 and ln 2 = ln2_hi + ln2_lo rounded to fp32 (ln2_hi has 16 significant bits,
+   * so k ln2_hi is exact for |k| < 2^8); the series coefficients 1/n! likewise */
+  const float inv_ln2 = 0x1.715476p+0f;
+  const float ln2_hi = 0x1.62e4p-1f;
+  const float ln2_lo = 0x1.7f7d1cp-20f;
   float t = xv * inv_ln2;
   t = t + 0.5f;
   const float kf = floorf(t);
   const int k = (int)kf;
   float r = xv - kf * ln2_hi;
   r = r - kf * ln2_lo;
-  float p = 1.0f / 720.0f;
+  float p = 0x1.6c16c2p-10f; /* 1/720 */
   p = p * r;
-  p = p + 1.0f / 120.0f;
+  p = p + 0x1.111112p-7f; /* 1/120 */
   p = p * r;
-  p = p + 1.0f / 24.0f;
+  p = p + 0x1.555556p-5f; /* 1/24 */
   p = p * r;
-  p = p + 1.0f / 6.0f;
+  p = p + 0x1.555556p-3f; /* 1/6 */
   p = p * r;
   p = p + 0.5f;
   p = p * r;
