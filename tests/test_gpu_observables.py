@@ -25,6 +25,7 @@ def _okw(kw):
     (2, (16, 16), 8, "packed"), (2, (40, 24), 33, "packed"), (3, (8, 8, 8), 12, "packed"),
     (3, (4, 6, 10), 70, "packed"), (3, (6, 6, 6), 12, "int8"), (2, (10, 4), 5, "int8"),
     (2, (8, 800), 4, "packed"),  # 32 lanes x 2 x 800 accumulators exceed shared memory
+    (2, (32, 12), 10, "packed"), (3, (24, 4, 4), 40, "packed"),  # half-rows of 16 and 12 sites
 ])
 def test_plane_sums_equal_oracle(oracle_mod, ndim, dims, T, fmt):
     kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.4, 2.0, T), sim_seed=12,
