@@ -292,9 +292,18 @@ __global__ void __launch_bounds__(QM_NT) k_qmodes_packed(Job jb, Dev dv, int Lma
   for (int r0 = 0; r0 < R; r0 += nr) {
     const int rows = min(nr, R - r0), n = rows * H;
     __syncthreads();
-    for (int e = threadIdx.x; e < W * 2 * n; e += QM_NT) {
-      const int w = e / (2 * n), rem = e - w * 2 * n, c = rem / n, i = rem - c * n;
-      tile[(size_t)w * tw + c * nr * H + i] = src[(size_t)w * g.N + c * g.Nh + r0 * H + i];
+    // 2W contiguous segments (plane w, colour c) of n words; 16-byte copies when the
+    // half-row length is a multiple of 4 words (then every segment starts 16-byte aligned)
+    for (int seg = 0; seg < 2 * W; ++seg) {
+      const int w = seg >> 1, c = seg & 1;
+      uint32_t *dst = tile + (size_t)w * tw + c * nr * H;
+      const uint32_t *from = src + (size_t)w * g.N + c * g.Nh + (size_t)r0 * H;
+      if ((H & 3) == 0) {
+        for (int i = threadIdx.x; i < (n >> 2); i += QM_NT)
+          reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(from)[i];
+      } else {
+        for (int i = threadIdx.x; i < n; i += QM_NT) dst[i] = from[i];
+      }
     }
     __syncthreads();
     for (int rr = warp; rr < rows; rr += QM_NT / 32) {
