@@ -55,7 +55,7 @@ __device__ __forceinline__ uint32_t word_of4(const uint4 &r, int i) {
 
 // Shared-memory map: spins, couplings, per-replica beta and energy sums, the chain's maps.
 struct GaussSmem {
-  int spin, jfix, betaf, eacc, pm, sl, pacc, near, bar, total;
+  int spin, jfix, betaf, eacc, pm, sl, pacc, accb, rejb, uw, slow, near, bar, total;
 };
 __host__ __device__ inline GaussSmem gauss_smem(int N, int d, int T, int Tp) {
   GaussSmem L;
@@ -66,38 +66,87 @@ __host__ __device__ inline GaussSmem gauss_smem(int N, int d, int T, int Tp) {
   L.pm = L.eacc + round16(8 * Tp);
   L.sl = L.pm + round16(4 * T);
   L.pacc = L.sl + round16(4 * T);
-  L.near = L.pacc + round16(4 * T);
+  L.accb = L.pacc + round16(4 * T); // exchange bounds, words and slow flags per pair
+  L.rejb = L.accb + round16(8 * T);
+  L.uw = L.rejb + round16(8 * T);
+  L.slow = L.uw + round16(4 * T);
+  L.near = L.slow + round16(T);
   L.bar = L.near + 16;
   L.total = L.bar + 16;
   return L;
 }
 
-// Replica exchange of one chain (Eq. 5) on int64 fixed-point energies, by one thread.
-__device__ void exchange_chain64(int T, const double *beta, int32_t *perm, int32_t *slot, const long long *E,
-                                 uint32_t s_glob, uint32_t c, uint32_t t, uint32_t k0, uint32_t k1,
-                                 unsigned int *pacc, unsigned int *pnear) {
-  for (int k = 0; k + 1 < T; ++k) {
-    const int a = perm[k], b = perm[k + 1];
-    const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
-    const double delta = __dmul_rn(dbeta, __dmul_rn((double)(E[a] - E[b]), 0x1p-20));
-    bool accept;
-    if (delta >= 0.0) {
-      accept = true;
-    } else {
-      const uint32_t u = philox10((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, k0, k1).x;
-      const double x = __dmul_rn((double)u, 0x1p-32);
-      const double e = exp(delta);
-      if (fabs(__dsub_rn(x, e)) < 1e-12) *pnear += 1u;
-      accept = x < e;
+// Replica exchange of one chain (Eq. 5) on int64 fixed-point energies, by one warp.  The
+// lanes first draw every pair's word u_k and turn the exact fp64 test into integer bounds
+// on dE = E_k - E_k+1 (fixed point) that are safe by a wide margin; the sequential pass
+// over k = 0..T-2 (lane 0) then compares integers, and only a decision inside the margin
+// (or u = 0) takes the exact path with the fp64 exp.  With x = u 2^-32 and
+// dbeta = beta_k - beta_k+1 > 0, the rule "accept iff delta >= 0 or x < exp(delta)",
+// delta = dbeta dE 2^-20, is for dE < 0 "dE 2^-20 > theta", theta = ln(x) / dbeta.  In
+// fp32, theta is within 5e-7 |theta| and the margin mg = max(4e-6 (1 + |theta|),
+// 1e-10 / (dbeta x)) covers that error many times, so dE 2^-20 >= theta + mg implies
+// exp(delta) >= x + 5e-11 and dE 2^-20 <= theta - mg implies x - exp(delta) >= 2.5e-11: both
+// agree with the fp64 test and lie outside the 1e-12 near-threshold window.  The bounds
+// are scaled by 2^20 and rounded outwards to integers (|theta| 2^20 < 2^62).
+__device__ void exchange_chain64_warp(int T, const double *beta, int32_t *perm, int32_t *slot, const long long *E,
+                                      long long *accb, long long *rejb, uint32_t *uw, uint8_t *slow,
+                                      uint32_t s_glob, uint32_t c, uint32_t t, uint32_t k0, uint32_t k1,
+                                      unsigned int *pacc, unsigned int *pnear) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k + 1 < T; k += 32) {
+    const uint32_t u = philox10((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, k0, k1).x;
+    const float dbeta = (float)__dsub_rn(beta[k], beta[k + 1]);
+    bool sl = u == 0u;
+    long long A = 0, R = 0;
+    if (!sl) {
+      const float x = (float)u * 0x1p-32f;
+      const float lnx = u > 0x80000000u ? log1pf(-(float)(0u - u) * 0x1p-32f) : logf(x);
+      const float theta = lnx / dbeta;
+      const float mg = fmaxf(4e-6f * (1.0f + fabsf(theta)), 1e-10f / (dbeta * x));
+      const float hi = (theta + mg) * 1048576.0f, lo = (theta - mg) * 1048576.0f;
+      const float LIM = 4.0e18f;
+      if (!(hi == hi) || !(lo == lo) || fabsf(hi) >= LIM || fabsf(lo) >= LIM) {
+        sl = true;
+      } else {
+        A = (long long)ceilf(hi);
+        R = (long long)floorf(lo);
+      }
     }
-    if (accept) {
-      pacc[k] += 1u;
-      perm[k] = b;
-      perm[k + 1] = a;
-      slot[a] = k + 1;
-      slot[b] = k;
+    accb[k] = A;
+    rejb[k] = R;
+    uw[k] = u;
+    slow[k] = sl ? 1 : 0;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int k = 0; k + 1 < T; ++k) {
+      const int a = perm[k], b = perm[k + 1];
+      const long long dE = E[a] - E[b];
+      bool accept;
+      if (dE >= 0) {
+        accept = true;
+      } else if (!slow[k] && dE >= accb[k]) {
+        accept = true;
+      } else if (!slow[k] && dE <= rejb[k]) {
+        accept = false;
+      } else {
+        const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
+        const double delta = __dmul_rn(dbeta, __dmul_rn((double)dE, 0x1p-20));
+        const double x = __dmul_rn((double)uw[k], 0x1p-32);
+        const double e = exp(delta);
+        if (fabs(__dsub_rn(x, e)) < 1e-12) *pnear += 1u;
+        accept = x < e;
+      }
+      if (accept) {
+        pacc[k] += 1u;
+        perm[k] = b;
+        perm[k + 1] = a;
+        slot[a] = k + 1;
+        slot[b] = k;
+      }
     }
   }
+  __syncwarp();
 }
 
 constexpr int GNT = 256;
@@ -116,6 +165,10 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
   int32_t *sl = reinterpret_cast<int32_t *>(smem + L.sl);
   unsigned int *pacc = reinterpret_cast<unsigned int *>(smem + L.pacc);
   unsigned int *pnear = reinterpret_cast<unsigned int *>(smem + L.near);
+  long long *accb = reinterpret_cast<long long *>(smem + L.accb);
+  long long *rejb = reinterpret_cast<long long *>(smem + L.rejb);
+  uint32_t *uw = reinterpret_cast<uint32_t *>(smem + L.uw);
+  uint8_t *slowf = smem + L.slow;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
 
   const int tid = threadIdx.x;
@@ -224,10 +277,10 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
       }
     }
     if (FUSE_PT) {
-      if (tid == 0) {
-        exchange_chain64(T, dv.beta, pm, sl, reinterpret_cast<const long long *>(eacc), s_glob, (uint32_t)c,
-                         t_pt0 + (uint32_t)m, jb.sk0, jb.sk1, pacc, pnear);
-        trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
+      if (tid < 32) {
+        exchange_chain64_warp(T, dv.beta, pm, sl, reinterpret_cast<const long long *>(eacc), accb, rejb, uw, slowf,
+                              s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb.sk0, jb.sk1, pacc, pnear);
+        if (tid == 0) trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
       }
       __syncthreads();
       if (!ENERGY_ONLY)
