@@ -90,6 +90,7 @@ def _load():
         lib.or_get_pt_stats.argtypes = [P, P, P]
         lib.or_get_class_stats.argtypes = [P, P, P]
         lib.or_set_counters.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        lib.or_set_houdayer_slots.argtypes = [P, ctypes.c_int]
         lib.or_run_binned.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, P]
         lib.or_enumerate.restype = ctypes.c_int
@@ -153,6 +154,7 @@ class OracleParams:
     p_plus: float = 0.5
     sim_seed: int = 1
     sample_offset: int = 0
+    houdayer_slots: int = 0  # the cluster move acts on slots k < houdayer_slots (0: every slot)
 
 
 class Oracle:
@@ -182,6 +184,10 @@ class Oracle:
         if not self._h:
             raise ValueError("oracle rejected the parameters")
         self._lib = lib
+        if p.houdayer_slots:
+            if not 0 <= int(p.houdayer_slots) <= self.T:
+                raise ValueError("houdayer_slots must lie in 0..n_temps")
+            lib.or_set_houdayer_slots(self._h, int(p.houdayer_slots))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -146,6 +146,7 @@ typedef struct {
   uint64_t *cls_tries; /* [T][d+1] */
   uint64_t *cls_acc;   /* [T][d+1] */
   uint64_t houd_moves, houd_flipped; /* moves with M > 0, total cluster sites    */
+  int houd_slots;      /* the cluster move acts on slots k < houd_slots (0: all)    */
   /* Round trips in temperature (the tunnelling time of Sec. 2.3), per replica j:   */
   int8_t *trip_dir;    /* [S][C][T] 0: no extreme seen, 1: bottom last, 2: top last */
   uint32_t *trip_t0;   /* [S][C][T] exchange pass of the trip's arrival at the bottom */
@@ -438,19 +439,32 @@ void or_get_trips(const or_state *st, uint32_t *n, uint64_t *sum) {
 /* ------------------------------------------------------------------------------ */
 /* Houdayer cluster move (Sec. 2.4, Eq. 10), one per (sample, temperature slot).  */
 /* ------------------------------------------------------------------------------ */
+/* The slots the move acts on: all T, or only the lowest houd_slots temperatures.      */
+/* Reading of the 3D modification that Secs. 1 and 2.4 point to (a manual cut of the    */
+/* effective cluster size): the move is kept to low temperatures, below the point where */
+/* q = -1 clusters percolate.  Pairs at other slots are left alone.                     */
+static int houd_kmax(const or_state *st) {
+  return (st->houd_slots > 0 && st->houd_slots < st->T) ? st->houd_slots : st->T;
+}
+
+void or_set_houdayer_slots(or_state *st, int k) {
+  if (k < 0 || k > st->T) st->error = 1;
+  else st->houd_slots = k;
+}
+
 void or_houdayer(or_state *st) {
   if (st->C < 2) {
     st->error = 1;
     return;
   }
-  const int N = st->N, d = st->ndim;
+  const int N = st->N, d = st->ndim, kmax = houd_kmax(st);
   const uint32_t t = st->t_houd;
   int8_t *q = (int8_t *)malloc((size_t)N);
   uint8_t *in = (uint8_t *)malloc((size_t)N);
   int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
   for (int s = 0; s < st->S; ++s) {
     uint32_t sg = (uint32_t)(st->s0 + s);
-    for (int k = 0; k < st->T; ++k) {
+    for (int k = 0; k < kmax; ++k) {
       int a = *at3(st->perm, st, s, 0, k);
       int b = *at3(st->perm, st, s, 1, k);
       int8_t *sa = spins_of(st, s, 0, a);
@@ -522,14 +536,14 @@ void or_houdayer_multi(or_state *st) {
     st->error = 1;
     return;
   }
-  const int N = st->N, d = st->ndim;
+  const int N = st->N, d = st->ndim, kmax = houd_kmax(st);
   const uint32_t t = st->t_houd;
   int8_t *q = (int8_t *)malloc((size_t)N);
   uint8_t *in = (uint8_t *)malloc((size_t)N);
   int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
   for (int s = 0; s < st->S; ++s) {
     uint32_t sg = (uint32_t)(st->s0 + s);
-    for (int k = 0; k < st->T; ++k) {
+    for (int k = 0; k < kmax; ++k) {
       int a = *at3(st->perm, st, s, 0, k);
       int b = *at3(st->perm, st, s, 1, k);
       int8_t *sa = spins_of(st, s, 0, a);

@@ -140,3 +140,18 @@ def test_infinite_temperature_flips_every_spin(oracle_mod):
     o.sweep(1)
     np.testing.assert_array_equal(o.spins(), 1 - s0)
     np.testing.assert_array_equal(o.energies(), e0)
+
+
+def test_low_temperature_houdayer_matches_enumeration(oracle_mod):
+    """Metropolis + PT + the move on the two lowest slots only still samples the
+    Boltzmann weights of Eq. 1's energy at every temperature."""
+    temps = [0.5, 0.8, 1.2, 1.8]
+    o = oracle_mod.Oracle(oracle_mod.OracleParams(2, (4, 4), 1, 2, temps, coupling_seed=1, sim_seed=9,
+                                                  houdayer_slots=2))
+    hist = o.enumerate(0)
+    o.mcs(2000, houdayer=True)
+    sE, sE2 = o.run_binned(120_000, 60, houdayer=True, pt=True)
+    check_against_enumeration(o, hist, temps, sE * 1.0, sE2 * 1.0, "2d4x4_pt_houdayer_low2")
+    assert o.check_energies() == 0
+    c = o.counters()
+    assert c["error"] == 0 and c["near_threshold"] == 0

@@ -243,3 +243,38 @@ def test_multicluster_move_flips_whole_components_by_coins(oracle_mod, ndim, dim
     assert n_comp > 200
     p = n_flip / n_comp
     assert abs(p - 0.5) < 4.5 * math.sqrt(0.25 / n_comp), (n_flip, n_comp)
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_houdayer_slot_restriction(oracle_mod, multi):
+    """The move restricted to the K lowest temperature slots equals the full move on the
+    pairs at slots k < K and leaves the pairs at k >= K alone; slots, not replica
+    indices, decide (the replica maps are scrambled by exchanges first)."""
+    temps = geometric_temps(0.3, 1.6, 8)
+    K = 3
+    full = make(oracle_mod, 2, (8, 6), 3, 2, temps, sim_seed=11)
+    low = make(oracle_mod, 2, (8, 6), 3, 2, temps, sim_seed=11, houdayer_slots=K)
+    full.mcs(40)
+    low.mcs(40)
+    before = full.spins()
+    assert np.array_equal(before, low.spins())
+    perm, _ = full.perm()
+    assert any(not np.array_equal(perm[s, c], np.arange(8)) for s in range(3) for c in range(2))
+    for o in (full, low):
+        o.houdayer_multi() if multi else o.houdayer()
+    sf, sl = full.spins(), low.spins()
+    moved_high = 0
+    expect_moves = 0
+    for s in range(3):
+        for k in range(8):
+            ja, jb = perm[s, 0, k], perm[s, 1, k]
+            if k < K:
+                assert np.array_equal(sl[s, 0, ja], sf[s, 0, ja]) and np.array_equal(sl[s, 1, jb], sf[s, 1, jb])
+                expect_moves += int(np.any(before[s, 0, ja] != before[s, 1, jb]))
+            else:
+                assert np.array_equal(sl[s, 0, ja], before[s, 0, ja]) and np.array_equal(sl[s, 1, jb], before[s, 1, jb])
+                moved_high += int(not np.array_equal(sf[s, 0, ja], before[s, 0, ja]))
+    assert moved_high > 0  # the full move did act on the excluded slots
+    c = low.counters()
+    assert c["houd_moves"] == expect_moves and c["error"] == 0
+    assert low.check_energies() == 0
