@@ -92,6 +92,12 @@ typedef struct {
                             pass (the tunnelling time of Sec. 2.3; see sg_trips); 0: off */
   int32_t coupling_kind; /* SG_COUPLINGS_PM or SG_COUPLINGS_FIXED (needs SG_INT8 spins and
                             houdayer == 0; SG_EUNSUPPORTED otherwise)                     */
+  int32_t houdayer_slots; /* 0: the Houdayer move (either variant) acts at every slot;
+                             K in 1..n_temps: only on the pairs at the K lowest
+                             temperature slots k < K, the others are left alone (the
+                             three-dimensional restriction that Secs. 1 and 2.4 point
+                             to: cluster moves kept below the temperature where q = -1
+                             clusters percolate); SG_EINVAL outside 0..n_temps         */
 } sg_params;
 
 /* Bytes of device memory a handle with these parameters needs. */

@@ -177,12 +177,20 @@ __device__ __forceinline__ void houd_tables(const Job &jb, const Dev &dv, int s,
   __syncthreads();
 }
 
+// The chain-0 lanes whose pair takes part in the move: a < T at a slot below hK.  A pair
+// outside it gets an empty q bitmap, hence M = 0 and no move.  Needs slot0 (phase 0).
+__device__ __forceinline__ uint32_t houd_pair_mask(const Job &jb, const int32_t *slot0) {
+  const int lane = threadIdx.x & 31;
+  return __ballot_sync(FULLM, lane < jb.T && slot0[lane] < jb.hK);
+}
+
 // Phase 1: the q bitmap of every pair of sample s (pair a's bitmap at Qb + a * NBW) and
 // its number M of q = -1 sites, added into Mc[a].  Warps stride over the 32-site blocks.
 __device__ __forceinline__ void houd_qmaps(const Job &jb, int RW, const uint32_t *w0p, const uint32_t *w1p,
-                                           const uint32_t *sig, uint32_t *Qb, int NBW, uint32_t *Mc) {
+                                           const uint32_t *sig, const int32_t *slot0, uint32_t *Qb, int NBW,
+                                           uint32_t *Mc) {
   const int T = jb.T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const uint32_t tmask = T >= 32 ? FULLM : ((1u << T) - 1u);
+  const uint32_t tmask = houd_pair_mask(jb, slot0);
   uint32_t mpart = 0u;
   for (int b = warp; b < NBW; b += nwarps) {
     bool valid;
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
   if (tid < 32) Mc[tid] = 0u;
   if (tid < 2) cnts[tid] = 0ull;
   houd_tables(jb, dv, s, perm0, perm1, slot0, slot1, sig, sigi);
-  houd_qmaps(jb, RW, w0w, w1w, sig, Qb, NBW, Mc);
+  houd_qmaps(jb, RW, w0w, w1w, sig, slot0, Qb, NBW, Mc);
   __syncthreads();
   for (int a = warp; a < T; a += HNT / 32) {
     const uint32_t M = Mc[a];
@@ -459,7 +467,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_q(Job jb, Dev dv, HoudSplit 
   const uint32_t *w0p = dv.spins + ((size_t)s * jb.W + 0) * jb.g.N;
   const uint32_t *w1p = dv.spins + ((size_t)s * jb.W + 1) * jb.g.N;
   uint32_t *Qb = hs.Qg + (size_t)s * T * NBW;
-  const uint32_t tmask = T >= 32 ? FULLM : ((1u << T) - 1u);
+  const uint32_t tmask = houd_pair_mask(jb, maps[2]);
   uint32_t mpart = 0u;
   for (int tb = blockIdx.y * HQ_TB; tb < NBW; tb += gridDim.y * HQ_TB) {
     const int nb = min(HQ_TB, NBW - tb);

@@ -71,6 +71,7 @@ sg_status validate(const sg_params *p) {
   if (p->houdayer && p->n_chains != 2) return SG_EINVAL;
   if (p->n_metro < 1 || (p->track_trips != 0 && p->track_trips != 1)) return SG_EINVAL;
   if (p->coupling_kind != SG_COUPLINGS_PM && p->coupling_kind != SG_COUPLINGS_FIXED) return SG_EINVAL;
+  if (p->houdayer_slots < 0 || p->houdayer_slots > p->n_temps) return SG_EINVAL;
   // general couplings: int8 spins (one replica per byte), no cluster move
   if (p->coupling_kind == SG_COUPLINGS_FIXED && (p->spin_format != SG_INT8 || p->houdayer != 0))
     return SG_EUNSUPPORTED;
@@ -97,6 +98,7 @@ void build_job(const sg_params *p, Job *jb) {
   jb->Wc = (p->n_temps + 31) / 32;
   jb->W = jb->C * jb->Wc;
   jb->Tp = (p->n_temps + 3) & ~3;
+  jb->hK = p->houdayer_slots > 0 ? p->houdayer_slots : p->n_temps;
   jb->sk0 = (uint32_t)(p->sim_seed & 0xFFFFFFFFu);
   jb->sk1 = (uint32_t)(p->sim_seed >> 32);
   jb->ck0 = (uint32_t)(p->coupling_seed & 0xFFFFFFFFu);
@@ -939,7 +941,7 @@ struct CkptHeader {
   uint64_t magic;
   uint32_t version, reserved;
   int32_t ndim, dims[3], n_samples, sample_offset, n_chains, n_temps, spin_format, houdayer, n_metro, track_trips,
-      coupling_kind, pad;
+      coupling_kind, houdayer_slots;
   uint64_t sim_seed, coupling_seed;
   double p_plus;
   uint64_t t_metro, t_pt, t_houd, device_bytes;
@@ -962,6 +964,7 @@ CkptHeader header_of(const sg_handle *h) {
   c.n_metro = h->p.n_metro;
   c.track_trips = h->p.track_trips;
   c.coupling_kind = h->p.coupling_kind;
+  c.houdayer_slots = h->p.houdayer_slots;
   c.sim_seed = h->p.sim_seed;
   c.coupling_seed = h->p.coupling_seed;
   c.p_plus = h->p.p_plus;

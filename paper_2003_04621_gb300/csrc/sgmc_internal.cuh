@@ -57,6 +57,7 @@ struct Geo {
 struct Job {
   Geo g;
   int S, s_off, C, T, Wc, W, Tp;
+  int hK;                  // the cluster move acts on the pairs at slots k < hK (<= T)
   uint32_t sk0, sk1;       // sim_seed as a Philox key
   uint32_t ck0, ck1;       // coupling_seed as a Philox key
   unsigned long long jcut; // J = +1 iff the word is below this (floor(p 2^32), up to 2^32)

@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("n_metro", ctypes.c_int32),
         ("track_trips", ctypes.c_int32),
         ("coupling_kind", ctypes.c_int32),
+        ("houdayer_slots", ctypes.c_int32),
     ]
 
 
@@ -127,8 +128,9 @@ def _check(status: int, where: str):
 def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, temps: Sequence[float],
                 coupling_seed: int = 1, sim_seed: int = 1, p_plus: float = 0.5, spin_format: str = "packed",
                 houdayer=False, n_metro: int = 1, sample_offset: int = 0, track_trips: bool = False,
-                couplings: str = "pm"):
-    """Fill an sg_params; returns (params, temps_array) -- keep the array alive."""
+                couplings: str = "pm", houdayer_slots: int = 0):
+    """Fill an sg_params; returns (params, temps_array) -- keep the array alive.
+    houdayer_slots: 0, or K to keep the cluster move to the K lowest temperature slots."""
     t = np.ascontiguousarray(np.asarray(temps, dtype=np.float64))
     p = Params()
     p.ndim = int(ndim)
@@ -149,6 +151,7 @@ def make_params(ndim: int, dims: Sequence[int], n_samples: int, n_chains: int, t
     if couplings not in ("pm", "fixed"):
         raise ValueError("couplings must be 'pm' (+-J from coupling_seed) or 'fixed' (set_couplings_fixed)")
     p.coupling_kind = 0 if couplings == "pm" else 1
+    p.houdayer_slots = int(houdayer_slots)
     return p, t
 
 
@@ -171,7 +174,7 @@ class Simulation:
 
     def __init__(self, ndim, dims, n_samples, n_chains, temps, coupling_seed=1, sim_seed=1, p_plus=0.5,
                  spin_format="packed", houdayer=False, n_metro=1, sample_offset=0, stream=None, device=None,
-                 device_buffer=None, track_trips=False, couplings="pm"):
+                 device_buffer=None, track_trips=False, couplings="pm", houdayer_slots=0):
         """device_buffer: optional (device pointer, bytes) the job lives in (256-byte
         aligned, at least query_bytes); by default a torch buffer is allocated."""
         import torch
@@ -185,7 +188,7 @@ class Simulation:
         self.S, self.C, self.T = int(n_samples), int(n_chains), len(temps)
         self.params, self._temps = make_params(ndim, dims, n_samples, n_chains, temps, coupling_seed, sim_seed,
                                                p_plus, spin_format, houdayer, n_metro, sample_offset,
-                                               track_trips, couplings)
+                                               track_trips, couplings, houdayer_slots)
         self.gauss = couplings == "fixed"
         self.bytes = query_bytes(self.params)
         if device_buffer is not None:

@@ -13,7 +13,7 @@ def oracle_of(oracle_mod, **kw):
     return oracle_mod.Oracle(oracle_mod.OracleParams(
         p["ndim"], p["dims"], p["n_samples"], p["n_chains"], list(p["temps"]),
         coupling_seed=p.get("coupling_seed", 1), p_plus=p.get("p_plus", 0.5), sim_seed=p.get("sim_seed", 1),
-        sample_offset=p.get("sample_offset", 0)))
+        sample_offset=p.get("sample_offset", 0), houdayer_slots=kw.get("houdayer_slots", 0)))
 
 
 def gpu_of(**kw):

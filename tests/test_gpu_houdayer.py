@@ -206,3 +206,20 @@ def run_pair_from(sim, orc, ops):
             sim.exchange()
             orc.exchange()
         assert_same_state(sim, orc, f"step {t} ({op})")
+
+
+# the move kept to the K lowest temperature slots (houdayer_slots = K): both kernels
+# (single-CTA and split), both variants, K below, at and (for 0) equal to T
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("K", [1, 3, 8])
+def test_houdayer_low_slots_2d(oracle_mod, K, split):
+    kw = dict(ndim=2, dims=(24, 16), n_samples=3, n_chains=2, temps=geometric_temps(0.2, 1.6, 8), sim_seed=23,
+              coupling_seed=3, houdayer=split, houdayer_slots=K)
+    run_pair(oracle_mod, kw, list("sxsxhsxhhx"))
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_houdayer_low_slots_mcs_3d(oracle_mod, multi):
+    kw = dict(ndim=3, dims=(8, 8, 8), n_samples=2, n_chains=2, temps=geometric_temps(0.5, 2.5, 12), sim_seed=29,
+              houdayer=2 if multi else True, houdayer_slots=4)
+    run_pair(oracle_mod, kw, ["m"] * 8)

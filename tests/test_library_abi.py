@@ -60,6 +60,8 @@ def test_parameter_validation_needs_no_gpu(libsgmc):
         (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0], couplings="fixed"), 5),  # packed
         (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0], couplings="fixed", spin_format="int8",
               houdayer=True), 5),
+        (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0, 2.0], houdayer=True, houdayer_slots=3), 1),
+        (dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=[1.0, 2.0], houdayer=True, houdayer_slots=-1), 1),
     ]
     for kw, want in cases:
         p, _t = sgmc.make_params(**kw)
