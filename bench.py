@@ -251,7 +251,8 @@ def bench_extensions(stream, steps: int = 5):
     """The rows beyond the core path, each timed with CUDA events on its own stream:
     the 2D L=128 Houdayer MCS with the single-cluster move and with the multi-cluster
     variant; the 2D L=16 Gaussian-coupling MCS; one overlap plane-sum measurement of the
-    3D L=16 job; the 3D L=16 MCS with round-trip counting on and off."""
+    3D L=16 job; the 3D L=16 MCS with round-trip counting on and off, and with the
+    cluster move on its 8 lowest temperature slots."""
     import torch
 
     from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer, workload_3d_l16
@@ -299,6 +300,13 @@ def bench_extensions(stream, steps: int = 5):
             qms = timed(lambda n: [sim.qmodes_device(P, stream=stream) for _ in range(n)], steps)
             out["qmodes_l16"] = {"ms_per_measurement": qms, "pairs": u.n_samples * u.T}
         sim.close()
+    # the 3D L=16 job with the cluster move kept to its 8 lowest temperatures (0.9-1.1)
+    sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), houdayer=True, houdayer_slots=8, stream=stream)
+    sim.set_launch(256, 2)
+    ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+    out["houdayer_3d_l16_low8"] = {"ms_per_mcs": ms, "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6),
+                                   "workload": u.name + "_houdayer_slots8"}
+    sim.close()
     return out
 
 
