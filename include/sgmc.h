@@ -151,6 +151,15 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
 /* As sg_measure, into DEVICE buffers of the same shapes, without synchronising. */
 sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
 
+/* As sg_measure into HOST buffers, but only enqueued on `stream`: the kernel and the two
+ * device-to-host copies run when the stream reaches them, so the host can queue the
+ * next steps at once.  The caller keeps the buffers alive and unread until it has
+ * synchronised the stream; page-locked (pinned) buffers let the copies run without
+ * blocking the host.  Later calls reuse the handle's device staging area in stream
+ * order, so each call may target its own host buffers.  A device-side error (a bulk-
+ * copy wait that ran out) is reported by the next call that synchronises. */
+sg_status sg_measure_async(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
+
 /* Round trips in temperature (Sec. 2.3: lowest -> highest -> lowest), counted after
  * every exchange pass t = 1, 2, ...: a replica at the lowest slot whose last extreme was
  * the highest completes a trip that began at its previous arrival at the lowest slot.

@@ -45,11 +45,6 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
   return x;
 }
 
-// Byte-table permutation of a word: out = OR over bytes of tab[byte index][byte value].
-__device__ __forceinline__ uint32_t permute_word(const uint32_t *tab, uint32_t w) {
-  return tab[w & 255u] | tab[256 + ((w >> 8) & 255u)] | tab[512 + ((w >> 16) & 255u)] | tab[768 + (w >> 24)];
-}
-
 // Runs of an L0-bit row (RW words, bits >= L0 zero).
 // fill_up: for every run of Q holding a bit of X (X subset of Q), the bits from its lowest
 // X bit to the run's top (the carry of Q + X runs through the run and stops above it).

@@ -2,6 +2,7 @@
 // couplings in plain layouts, and the measurement of E by slot and N q (Eqs. 3-4).
 #include "sgmc_internal.cuh"
 #include "sgmc_tma.cuh"
+#include "sgmc_sweep.cuh"
 
 namespace sgmc {
 
@@ -250,6 +251,76 @@ __global__ void __launch_bounds__(OV_NT) k_overlap_packed(Job jb, Dev dv, int tl
   }
 }
 
+// Both observables of a two-chain packed job whose chains are one word each (T <= 32),
+// in one pass per sample: E by slot and N q per slot (Eqs. 3-4).  One CTA per sample.
+// The chain-1 word is permuted into chain-0 lane order (bit b moves to lane
+// perm0[slot1[b]], the chain-0 replica at the same temperature), so bit a of
+// w0 ^ sigma(w1) is 1 iff the pair of chain-0 replica a disagrees at that site.  Four
+// sites' disagreement words are compressed to a 3-bit value and added into bit-sliced
+// counters, 32 pairs per instruction; the warp sums its counters by butterfly before
+// they can overflow (8 planes: at most 63 iterations of 4 sites).
+constexpr int MP_NT = 256;
+
+__global__ void __launch_bounds__(MP_NT) k_measure_pairs_w1(Job jb, Dev dv, int32_t *E_out, int32_t *Q_out) {
+  __shared__ uint32_t sig[1024];
+  __shared__ int32_t maps[4][32]; // perm0, perm1, slot0, slot1
+  __shared__ uint32_t tot[32];    // disagreeing sites of the pair of chain-0 replica a
+  const int s = blockIdx.x, T = jb.T, tid = threadIdx.x, lane = tid & 31;
+  const size_t c0 = (size_t)s * 2 * T;
+  if (tid < 32) {
+    maps[0][tid] = tid < T ? dv.perm[c0 + tid] : 0;
+    maps[1][tid] = tid < T ? dv.perm[c0 + T + tid] : 0;
+    maps[2][tid] = tid < T ? dv.slot[c0 + tid] : 0;
+    maps[3][tid] = tid < T ? dv.slot[c0 + T + tid] : 0;
+    tot[tid] = 0u;
+  }
+  __syncthreads();
+  for (int e = tid; e < 1024; e += MP_NT) {
+    const int j = e >> 8, v = e & 255;
+    uint32_t o = 0u;
+#pragma unroll
+    for (int bb = 0; bb < 8; ++bb) {
+      const int b = 8 * j + bb;
+      if (((v >> bb) & 1) && b < T) o |= 1u << maps[0][maps[3][b]];
+    }
+    sig[e] = o;
+  }
+  if (E_out)
+    for (int e = tid; e < 2 * T; e += MP_NT) {
+      const int c = e >= T ? 1 : 0;
+      E_out[c0 + e] = dv.E[c0 + (size_t)c * T + maps[c][e - c * T]];
+    }
+  __syncthreads();
+  if (!Q_out) return;
+  const int N = jb.g.N, n4 = N >> 2; // every extent is even, so N is a multiple of 4
+  const uint4 *p0 = reinterpret_cast<const uint4 *>(dv.spins + (size_t)s * jb.W * N);
+  const uint4 *p1 = p0 + n4;
+  uint32_t V[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) V[b] = 0u;
+  const int iters = (n4 + MP_NT - 1) / MP_NT;
+  for (int it = 0; it < iters; ++it) {
+    const int i = it * MP_NT + tid;
+    if (i < n4) {
+      const uint4 a = p0[i], b = p1[i];
+      const uint32_t q0 = a.x ^ permute_word(sig, b.x), q1 = a.y ^ permute_word(sig, b.y);
+      const uint32_t q2 = a.z ^ permute_word(sig, b.z), q3 = a.w ^ permute_word(sig, b.w);
+      uint32_t s1, cy1;
+      fadd(q0, q1, q2, s1, cy1);
+      const uint32_t cc = s1 & q3;
+      vcount_add(V, s1 ^ q3, cy1 ^ cc, cy1 & cc);
+    }
+    if ((it + 1) % 63 == 0 || it + 1 == iters) { // warp-uniform
+      const int32_t v = warp_lane_sum(V);
+      if (v) atomicAdd(&tot[lane], (uint32_t)v);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) V[b] = 0u;
+    }
+  }
+  __syncthreads();
+  if (tid < T) Q_out[(size_t)s * T + maps[2][tid]] = N - 2 * (int32_t)tot[tid];
+}
+
 // ---------------------------------------------------------------------------------
 // Overlap plane sums (the integer part of the Fourier modes of q behind chi_SG and the
 // correlation length, two-replica measurements of Sec. 3): P[s][k][mu][x] = sum of
@@ -471,6 +542,10 @@ cudaError_t launch_import_couplings(const Job &jb, const Dev &dv, const int8_t *
 
 cudaError_t launch_measure(const Job &jb, const Dev &dv, bool int8fmt, int32_t *E_out, int32_t *Q_out,
                            cudaStream_t st) {
+  if (!int8fmt && jb.C == 2 && jb.Wc == 1 && Q_out) {
+    k_measure_pairs_w1<<<(unsigned)jb.S, MP_NT, 0, st>>>(jb, dv, E_out, Q_out);
+    return cudaGetLastError();
+  }
   k_gather_energy<<<blocks_for((long long)jb.S * jb.C * jb.T, 256), 256, 0, st>>>(jb, dv, E_out);
   if (Q_out && jb.C >= 2) {
     if (int8fmt) k_overlap_int8<<<(unsigned)(jb.S * jb.T), 256, 0, st>>>(jb, dv, Q_out);

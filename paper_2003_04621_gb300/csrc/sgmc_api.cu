@@ -704,7 +704,7 @@ sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintpt
   return check(h, launch_measure(h->job, h->dev, h->int8fmt != 0, E_out, Q_out, st));
 }
 
-sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
+sg_status sg_measure_async(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
   if (!h || !E_out) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
   if (h->gauss) return SG_EUNSUPPORTED;
@@ -717,8 +717,13 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
   const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
   cudaError_t e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return check(h, e);
-  return poll_device_error(h, st);
+  return check(h, e);
+}
+
+sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
+  const sg_status r = sg_measure_async(h, E_out, Q_out, stream);
+  if (r != SG_OK) return r;
+  return poll_device_error(h, as_stream(stream));
 }
 
 sg_status sg_trips(sg_handle *h, uint32_t *n_out, uint64_t *sum_out, uintptr_t stream) {

@@ -280,6 +280,11 @@ __device__ __forceinline__ int nbr_cs(const Geo &g, const SiteGeo &s, int mu, in
   return base + (s.y + g.L1 * z2) * g.H + s.k;
 }
 
+// Byte-table permutation of a word: out = OR over bytes of tab[byte index][byte value].
+__device__ __forceinline__ uint32_t permute_word(const uint32_t *tab, uint32_t w) {
+  return tab[w & 255u] | tab[256 + ((w >> 8) & 255u)] | tab[512 + ((w >> 16) & 255u)] | tab[768 + (w >> 24)];
+}
+
 // Bit-sliced full adder: sum and carry of three 32-lane bit planes.
 __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy) {
   s = a ^ b ^ c;

@@ -60,3 +60,42 @@ def test_plane_sums_need_two_chains():
     with pytest.raises(SGError) as e:
         sim.qmodes()
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("ndim,dims,T", [(2, (256, 256), 5), (3, (48, 48, 48), 32), (2, (2, 2), 3)])
+def test_single_pass_measurement_large_lattices(oracle_mod, ndim, dims, T):
+    """E by slot and N q of chains of one word come from one pass per sample whose
+    bit-sliced counters are summed every 63 iterations: lattices of 65,536 and 110,592
+    sites run several such flushes (and the 4-site lattice a partial warp)."""
+    kw = dict(ndim=ndim, dims=dims, n_samples=2, n_chains=2, temps=geometric_temps(0.4, 2.0, T), sim_seed=31,
+              coupling_seed=8)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    for t in range(2):
+        sim.run_mcs(1)
+        orc.mcs(1)
+        E_g, Q_g = sim.measure()
+        E_o, Q_o = orc.measure()
+        np.testing.assert_array_equal(E_g, E_o, err_msg=f"E, mcs {t + 1}")
+        np.testing.assert_array_equal(Q_g, Q_o, err_msg=f"N q, mcs {t + 1}")
+
+
+def test_asynchronous_measurement_ring(oracle_mod):
+    """sg_measure_async: one read per MCS into its own slot of a pinned ring, queued
+    behind the MCS without synchronising; every slot equals the oracle's measurement
+    after the same number of MCS."""
+    import torch
+
+    kw = dict(ndim=3, dims=(8, 8, 8), n_samples=3, n_chains=2, temps=geometric_temps(0.5, 2.0, 12), sim_seed=41)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    n = 4
+    E = torch.empty((n, 3, 2, 12), dtype=torch.int32, pin_memory=True).numpy()
+    Q = torch.empty((n, 3, 12), dtype=torch.int32, pin_memory=True).numpy()
+    for k in range(n):
+        sim.run_mcs(1)
+        sim.measure_async(E[k], Q[k])
+    torch.cuda.synchronize()
+    for k in range(n):
+        orc.mcs(1)
+        E_o, Q_o = orc.measure()
+        np.testing.assert_array_equal(E[k], E_o, err_msg=f"E slot {k}")
+        np.testing.assert_array_equal(Q[k], Q_o, err_msg=f"N q slot {k}")
