@@ -252,7 +252,7 @@ def bench_extensions(stream, steps: int = 5):
     the 2D L=128 Houdayer MCS with the single-cluster move and with the multi-cluster
     variant; the 2D L=16 Gaussian-coupling MCS; one overlap plane-sum measurement of the
     3D L=16 job; the 3D L=16 MCS with round-trip counting on and off, and with the
-    cluster move on its 8 lowest temperature slots."""
+    cluster move on its 8 lowest temperature slots; Metropolis sweeps alone."""
     import torch
 
     from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer, workload_3d_l16
@@ -296,6 +296,10 @@ def bench_extensions(stream, steps: int = 5):
         out["mcs_trips_on" if track else "mcs_trips_off"] = {"ms_per_mcs": ms,
                                                              "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6)}
         if not track:
+            # Metropolis alone (the paper's per-update time), same resident kernel without
+            # the exchange passes
+            ms_sw = timed(lambda n: sim.sweep(n, stream=stream), steps)
+            out["metropolis_only_l16"] = {"ms_per_sweep": ms_sw, "attempts_per_ns": u.attempts_per_sweep / (ms_sw * 1e6)}
             P = torch.empty((u.n_samples, u.T, 3, 16), dtype=torch.int32, device="cuda")
             qms = timed(lambda n: [sim.qmodes_device(P, stream=stream) for _ in range(n)], steps)
             out["qmodes_l16"] = {"ms_per_measurement": qms, "pairs": u.n_samples * u.T}

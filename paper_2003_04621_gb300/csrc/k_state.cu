@@ -259,10 +259,11 @@ __global__ void __launch_bounds__(OV_NT) k_overlap_packed(Job jb, Dev dv, int tl
 // sites' disagreement words are compressed to a 3-bit value and added into bit-sliced
 // counters, 32 pairs per instruction; the warp sums its counters by butterfly before
 // they can overflow (8 planes: at most 63 iterations of 4 sites).
-constexpr int MP_NT = 256;
+constexpr int MP_NT = 128;
 
 __global__ void __launch_bounds__(MP_NT) k_measure_pairs_w1(Job jb, Dev dv, int32_t *E_out, int32_t *Q_out) {
   __shared__ uint32_t sig[1024];
+  __shared__ uint32_t nib[128];   // the same permutation by nibbles: [nibble][value]
   __shared__ int32_t maps[4][32]; // perm0, perm1, slot0, slot1
   __shared__ uint32_t tot[32];    // disagreeing sites of the pair of chain-0 replica a
   const int s = blockIdx.x, T = jb.T, tid = threadIdx.x, lane = tid & 31;
@@ -275,15 +276,20 @@ __global__ void __launch_bounds__(MP_NT) k_measure_pairs_w1(Job jb, Dev dv, int3
     tot[tid] = 0u;
   }
   __syncthreads();
-  for (int e = tid; e < 1024; e += MP_NT) {
-    const int j = e >> 8, v = e & 255;
+  for (int e = tid; e < 128; e += MP_NT) {
+    const int j = e >> 4, v = e & 15;
     uint32_t o = 0u;
 #pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
-      const int b = 8 * j + bb;
+    for (int bb = 0; bb < 4; ++bb) {
+      const int b = 4 * j + bb;
       if (((v >> bb) & 1) && b < T) o |= 1u << maps[0][maps[3][b]];
     }
-    sig[e] = o;
+    nib[e] = o;
+  }
+  __syncthreads();
+  for (int e = tid; e < 1024; e += MP_NT) {
+    const int j = e >> 8, v = e & 255;
+    sig[e] = nib[(2 * j) * 16 + (v & 15)] | nib[(2 * j + 1) * 16 + (v >> 4)];
   }
   if (E_out)
     for (int e = tid; e < 2 * T; e += MP_NT) {
