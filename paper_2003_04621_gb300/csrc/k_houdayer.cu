@@ -31,20 +31,6 @@ namespace {
 constexpr uint32_t FULLM = 0xFFFFFFFFu;
 constexpr int HNT = 1024; // threads per CTA (32 warps)
 
-// In-warp 32x32 bit transpose: afterwards lane l holds bit i = (input of lane i, bit l).
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int j = 16 >> st;
-    const uint32_t m = masks[st];
-    const uint32_t y = __shfl_xor_sync(FULLM, x, j);
-    if (lane & j) x = (x & ~m) | ((y & ~m) >> j);
-    else x = (x & m) | ((y & m) << j);
-  }
-  return x;
-}
-
 // Runs of an L0-bit row (RW words, bits >= L0 zero).
 // fill_up: for every run of Q holding a bit of X (X subset of Q), the bits from its lowest
 // X bit to the run's top (the carry of Q + X runs through the run and stops above it).

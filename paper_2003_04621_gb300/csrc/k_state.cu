@@ -411,6 +411,176 @@ __global__ void __launch_bounds__(QM_NT) k_qmodes_packed(Job jb, Dev dv, int Lma
   }
 }
 
+// Two-chain packed jobs whose chains are one word each (T <= 32): one CTA per sample.
+// The disagreement words d = w0 ^ sigma(w1) of 32 sites (sigma as in k_measure_pairs_w1)
+// are transposed across the warp, so that lane a holds the disagreements of the pair of
+// chain-0 replica a at the step's 32 sites, bit t for the site of lane t.  A step covers
+// `rps` whole rows when L0 <= 32 (lane t: row t / L0, x = t % L0), else a 32-site chunk
+// of one row, the warp's chunk fixed.  A row's popcount is its count, added to its y and
+// z planes.  Bit-sliced counters over the steps hold the count of each bit position, i.e.
+// of each x, until they are emptied (every 255 steps and at the end).
+// P = (sites in the plane) - 2 (disagreements).
+constexpr int QW_NT = 256;
+
+// r / d for 0 <= r < 2^26 by a multiply-high with m = ceil((2^32 - 1) / d) (an estimate
+// off by at most one) and one correction each way.
+__device__ __forceinline__ int div_by(int r, int d, uint32_t m) {
+  int q = (int)__umulhi((uint32_t)r, m);
+  q += (q + 1) * d <= r ? 1 : 0;
+  q -= q * d > r ? 1 : 0;
+  return q;
+}
+
+// Empty a lane's bit-sliced x-plane counters into its pair's accumulators: bit t counts
+// the site of lane t (x = t mod L0 for rows of at most 32 sites, else 32 chunk + t).
+// The planes in use (those below the warp's highest nonzero one) are summed per x
+// first, so each x takes one atomic add.
+__device__ __forceinline__ void qw_flush(uint32_t (&V)[NB], bool narrow, int L0, uint32_t rep, int chunk,
+                                         uint32_t *drow) {
+  int nb = 0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) nb = __any_sync(0xFFFFFFFFu, V[b] != 0u) ? b + 1 : nb;
+  if (narrow) {
+    for (int xx = 0; xx < L0; ++xx) {
+      uint32_t c = 0u;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (b < nb) c += (uint32_t)__popc(V[b] & (rep << xx)) << b;
+      if (c) atomicAdd(&drow[xx], c);
+    }
+  } else {
+    for (int t = 0; t < 32 && 32 * chunk + t < L0; ++t) {
+      uint32_t c = 0u;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) c |= ((V[b] >> t) & 1u) << b;
+      if (c) atomicAdd(&drow[32 * chunk + t], c);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) V[b] = 0u;
+}
+
+template <int D>
+__global__ void __launch_bounds__(QW_NT, 4) k_qmodes_w1(Job jb, Dev dv, int Lmax, int32_t *P_out) {
+  extern __shared__ __align__(16) uint32_t qw_smem[];
+  uint32_t *sig = qw_smem;                                  // [1024]
+  uint32_t *nib = sig + 1024;                               // [128]
+  int32_t *maps = reinterpret_cast<int32_t *>(nib + 128);   // [4][32] perm0, perm1, slot0, slot1
+  const int stride = D * Lmax + 1;                          // per pair; odd, so lanes hit 32 banks
+  uint32_t *dis = reinterpret_cast<uint32_t *>(maps + 128); // [32][stride]
+  const Geo g = jb.g;
+  const int s = blockIdx.x, T = jb.T, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int L0 = g.L0, L1 = g.L1, H = g.H, R = g.R, Nh = g.Nh, N = g.N;
+  const size_t c0 = (size_t)s * 2 * T;
+  if (tid < 32) {
+    maps[tid] = tid < T ? dv.perm[c0 + tid] : 0;
+    maps[32 + tid] = tid < T ? dv.perm[c0 + T + tid] : 0;
+    maps[64 + tid] = tid < T ? dv.slot[c0 + tid] : 0;
+    maps[96 + tid] = tid < T ? dv.slot[c0 + T + tid] : 0;
+  }
+  for (int i = tid; i < 32 * stride; i += QW_NT) dis[i] = 0u;
+  __syncthreads();
+  for (int e = tid; e < 128; e += QW_NT) {
+    const int j = e >> 4, v = e & 15;
+    uint32_t o = 0u;
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      const int b = 4 * j + bb;
+      if (((v >> bb) & 1) && b < T) o |= 1u << maps[maps[96 + b]];
+    }
+    nib[e] = o;
+  }
+  __syncthreads();
+  for (int e = tid; e < 1024; e += QW_NT) {
+    const int j = e >> 8, v = e & 255;
+    sig[e] = nib[(2 * j) * 16 + (v & 15)] | nib[(2 * j + 1) * 16 + (v >> 4)];
+  }
+  __syncthreads();
+
+  const uint32_t *w0 = dv.spins + (size_t)s * jb.W * N, *w1 = w0 + N;
+  const bool narrow = L0 <= 32;
+  const int rps = narrow ? 32 / L0 : 1;            // rows per step
+  const int nch = narrow ? 1 : (L0 + 31) >> 5;     // chunks per row
+  const int nw = QW_NT / 32;
+  const int wpc = narrow ? nw : nw / nch;          // warps per chunk (launcher: nch <= nw)
+  const bool active = narrow || warp < wpc * nch;
+  const int chunk = narrow ? 0 : warp % nch;
+  const int step0 = narrow ? warp : warp / nch;    // first row group of this warp
+  const int sstride = narrow ? nw : wpc;
+  const int nsteps = narrow ? (R + rps - 1) / rps : R;
+  const uint32_t segmask = L0 >= 32 ? 0xFFFFFFFFu : ((1u << L0) - 1u);
+  uint32_t rep = 0u; // one bit per row of a step, at the row's first lane
+  for (int j = 0; j < rps; ++j) rep |= 1u << (j * L0);
+  // this lane's site within a step
+  const int jrow = narrow ? lane / L0 : 0;
+  const int x = narrow ? lane - jrow * L0 : 32 * chunk + lane;
+  const bool lane_ok = narrow ? jrow < rps : x < L0;
+  const uint32_t mL1 = (uint32_t)((0xFFFFFFFFull + L1) / (unsigned)L1);
+  uint32_t V[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) V[b] = 0u;
+  int since = 0;
+  uint32_t *drow = dis + lane * stride; // this lane's pair
+  constexpr int U = 4; // steps whose words are loaded before any is used
+  if (active) {
+    for (int st0 = step0; st0 < nsteps; st0 += U * sstride) {
+      uint32_t a[U], bw[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int st = st0 + u * sstride;
+        const int r = narrow ? st * rps + jrow : st;
+        a[u] = bw[u] = 0u;
+        if (st < nsteps && lane_ok && r < R) {
+          const int z = div_by(r, L1, mL1), y = r - z * L1;
+          const int p = ((x & 1) ^ ((y + z) & 1)) * Nh + r * H + (x >> 1);
+          a[u] = w0[p];
+          bw[u] = w1[p];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int st = st0 + u * sstride;
+        if (st >= nsteps) break; // warp-uniform
+        // empty words permute to 0, so lanes without a site give 0
+        const uint32_t X = transpose32(a[u] ^ permute_word(sig, bw[u]), lane);
+        // rows: y and z planes
+        for (int j = 0; j < rps; ++j) {
+          const int rr = narrow ? st * rps + j : st;
+          if (rr >= R) break;
+          const uint32_t cnt = __popc(narrow ? (X >> (j * L0)) & segmask : X);
+          if (cnt) {
+            const int z = div_by(rr, L1, mL1);
+            atomicAdd(&drow[Lmax + rr - z * L1], cnt);
+            if (D == 3) atomicAdd(&drow[2 * Lmax + z], cnt);
+          }
+        }
+        // x planes: add X into the bit-sliced counters (one plane carries into the next)
+        uint32_t cy = X;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const uint32_t t2 = V[b] & cy;
+          V[b] ^= cy;
+          cy = t2;
+        }
+        if (++since == 255) { // NB = 8 planes hold up to 255 per bit
+          qw_flush(V, narrow, L0, rep, chunk, drow);
+          since = 0;
+        }
+      }
+    }
+    qw_flush(V, narrow, L0, rep, chunk, drow);
+  }
+  __syncthreads();
+  // slot k's pair is the one of chain-0 replica perm0[k]
+  for (int e = tid; e < T * D * Lmax; e += QW_NT) {
+    const int k = e / (D * Lmax), i = e - k * (D * Lmax);
+    const int mu = i / Lmax, xx = i - mu * Lmax;
+    const int Lmu = mu == 0 ? L0 : (mu == 1 ? L1 : g.L2);
+    P_out[((size_t)s * T + k) * D * Lmax + i] =
+        xx < Lmu ? N / Lmu - 2 * (int32_t)dis[maps[k] * stride + i] : 0;
+  }
+}
+
 // int8 layout: CTA per (sample, slot); shared-memory accumulators, atomics per site.
 __global__ void __launch_bounds__(256) k_qmodes_int8(Job jb, Dev dv, int Lmax, int32_t *P_out) {
   extern __shared__ __align__(16) uint32_t qm_smem[];
@@ -449,6 +619,8 @@ void qmodes_shape(const Job &jb, int Lmax, int *nr, size_t *smem, bool *gacc) {
   *smem = (size_t)n * per_row + (*gacc ? 0 : accb);
 }
 
+size_t qmodes_w1_smem(int d, int Lmax) { return (1024 + 128 + 128) * 4 + (size_t)32 * (d * Lmax + 1) * 4; }
+
 int qmodes_lmax(const Job &jb) {
   int m = jb.g.L0;
   if (jb.g.L1 > m) m = jb.g.L1;
@@ -461,6 +633,14 @@ cudaError_t launch_qmodes(const Job &jb, const Dev &dv, bool int8fmt, int32_t *P
   const int Lmax = qmodes_lmax(jb);
   if (int8fmt) {
     k_qmodes_int8<<<(unsigned)(jb.S * jb.T), 256, (size_t)jb.g.d * Lmax * 4, st>>>(jb, dv, Lmax, P_out);
+    return cudaGetLastError();
+  }
+  // chains of one word: the transposed single pass, while its counters fit shared memory
+  // and a row has at most one 32-site chunk per warp
+  const size_t wsm = qmodes_w1_smem(jb.g.d, Lmax);
+  if (jb.C == 2 && jb.Wc == 1 && wsm <= 96 * 1024 && (jb.g.L0 + 31) / 32 <= QW_NT / 32) {
+    if (jb.g.d == 2) k_qmodes_w1<2><<<(unsigned)jb.S, QW_NT, wsm, st>>>(jb, dv, Lmax, P_out);
+    else k_qmodes_w1<3><<<(unsigned)jb.S, QW_NT, wsm, st>>>(jb, dv, Lmax, P_out);
     return cudaGetLastError();
   }
   int nr;
@@ -479,9 +659,9 @@ cudaError_t launch_qmodes(const Job &jb, const Dev &dv, bool int8fmt, int32_t *P
 }
 
 cudaError_t prepare_state_kernels(int max_smem) {
-  const void *fns[5] = {(const void *)k_qmodes_packed<2, false>, (const void *)k_qmodes_packed<2, true>,
+  const void *fns[7] = {(const void *)k_qmodes_packed<2, false>, (const void *)k_qmodes_packed<2, true>,
                         (const void *)k_qmodes_packed<3, false>, (const void *)k_qmodes_packed<3, true>,
-                        (const void *)k_qmodes_int8};
+                        (const void *)k_qmodes_int8, (const void *)k_qmodes_w1<2>, (const void *)k_qmodes_w1<3>};
   for (const void *fn : fns) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;

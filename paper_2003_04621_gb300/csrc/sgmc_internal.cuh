@@ -280,6 +280,20 @@ __device__ __forceinline__ int nbr_cs(const Geo &g, const SiteGeo &s, int mu, in
   return base + (s.y + g.L1 * z2) * g.H + s.k;
 }
 
+// In-warp 32x32 bit transpose: afterwards lane l holds bit i = (input of lane i, bit l).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int j = 16 >> st;
+    const uint32_t m = masks[st];
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+    if (lane & j) x = (x & ~m) | ((y & ~m) >> j);
+    else x = (x & m) | ((y & m) << j);
+  }
+  return x;
+}
+
 // Byte-table permutation of a word: out = OR over bytes of tab[byte index][byte value].
 __device__ __forceinline__ uint32_t permute_word(const uint32_t *tab, uint32_t w) {
   return tab[w & 255u] | tab[256 + ((w >> 8) & 255u)] | tab[512 + ((w >> 16) & 255u)] | tab[768 + (w >> 24)];

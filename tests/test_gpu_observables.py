@@ -26,6 +26,10 @@ def _okw(kw):
     (3, (4, 6, 10), 70, "packed"), (3, (6, 6, 6), 12, "int8"), (2, (10, 4), 5, "int8"),
     (2, (8, 800), 4, "packed"),  # 32 lanes x 2 x 800 accumulators exceed shared memory
     (2, (32, 12), 10, "packed"), (3, (24, 4, 4), 40, "packed"),  # half-rows of 16 and 12 sites
+    # one-word chains, transposed pass: rows of 6 (5 rows per step, 2 idle lanes), 2 and
+    # 40 sites; rows of 96, 128 and 256 sites in 3, 4 and 8 chunks
+    (2, (6, 10), 7, "packed"), (3, (2, 6, 4), 9, "packed"), (3, (40, 4, 6), 16, "packed"),
+    (2, (96, 16), 8, "packed"), (2, (128, 128), 24, "packed"), (2, (256, 8), 5, "packed"),
 ])
 def test_plane_sums_equal_oracle(oracle_mod, ndim, dims, T, fmt):
     kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.4, 2.0, T), sim_seed=12,
@@ -99,3 +103,17 @@ def test_asynchronous_measurement_ring(oracle_mod):
         E_o, Q_o = orc.measure()
         np.testing.assert_array_equal(E[k], E_o, err_msg=f"E slot {k}")
         np.testing.assert_array_equal(Q[k], Q_o, err_msg=f"N q slot {k}")
+
+
+
+@pytest.mark.parametrize("dims,T", [((32, 64, 64), 4), ((64, 64, 64), 3)])
+def test_plane_sums_counter_flushes(oracle_mod, dims, T):
+    """Chains of one word on lattices where a warp takes more than 255 steps, so its
+    bit-sliced x-plane counters are emptied during the pass (rows of 32 sites, one step
+    each; rows of 64 sites in two chunks)."""
+    kw = dict(ndim=3, dims=dims, n_samples=1, n_chains=2, temps=geometric_temps(0.6, 1.8, T), sim_seed=5,
+              coupling_seed=6)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    sim.run_mcs(2)
+    orc.mcs(2)
+    np.testing.assert_array_equal(sim.qmodes(), orc.qmodes())
