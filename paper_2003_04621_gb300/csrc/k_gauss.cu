@@ -209,6 +209,11 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
   }
 
   const int H = g.H, L1 = g.L1, Nh = g.Nh;
+  const uint32_t mH = div_magic(H), mL1 = div_magic(L1 < 2 ? 2 : L1);
+  // when G divides the CTA, a thread keeps one replica group gi = tid % G and walks the
+  // sites q = tid / G, tid / G + GNT / G, ...; its energy terms stay in registers and are
+  // summed over the warp's lanes of the same group before one shared add each
+  const bool fixed_g = (GNT % G) == 0;
   const int n_outer = ENERGY_ONLY ? 1 : n_mcs;
   const int n_inner = ENERGY_ONLY ? 1 : n_metro;
   for (int m = 0; m < n_outer; ++m) {
@@ -219,15 +224,18 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
           for (int j = tid; j < Tp; j += GNT) eacc[j] = 0ull;
           __syncthreads();
         }
-        for (int it = tid; it < Nh * G; it += GNT) {
-          const int q = it / G;
-          const int gi = it - q * G;
+        long long el[4] = {0, 0, 0, 0};
+        const int gfix = fixed_g ? tid % G : 0, qstep = fixed_g ? GNT / G : 0;
+        int qf = fixed_g ? tid / G : 0;
+        for (int it = tid; it < Nh * G; it += GNT, qf += qstep) {
+          const int q = fixed_g ? qf : it / G;
+          const int gi = fixed_g ? gfix : it - q * G;
           SiteGeo sg;
           sg.c = col;
-          sg.row = q / H;
+          sg.row = div_by(q, H, mH);
           sg.k = q - sg.row * H;
-          sg.y = D == 3 ? sg.row % L1 : sg.row;
-          sg.z = D == 3 ? sg.row / L1 : 0;
+          sg.z = D == 3 ? div_by(sg.row, L1, mL1) : 0;
+          sg.y = D == 3 ? sg.row - sg.z * L1 : sg.row;
           sg.xodd = col ^ ((sg.y + sg.z) & 1);
           const int p = col * Nh + q;
           char4 s4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)p * Tp + 4 * gi);
@@ -268,10 +276,27 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
           }
           if (col == 1) {
             // every bond has exactly one colour-1 end: E = -sum over colour-1 sites of s h
+            if (fixed_g) {
+#pragma unroll
+              for (int r = 0; r < 4; ++r) el[r] -= (long long)sv[r] * h[r];
+            } else {
+#pragma unroll
+              for (int r = 0; r < 4; ++r)
+                if (4 * gi + r < T) atomicAdd(&eacc[4 * gi + r], (unsigned long long)(-(long long)sv[r] * h[r]));
+            }
+          }
+        }
+        if (col == 1 && fixed_g) {
+          // lanes l and l ^ o hold the same group for o a multiple of G (G | 32), else
+          // every lane of the warp has its own group
+          if (G < 32)
+            for (int o = 16; o >= G; o >>= 1)
+#pragma unroll
+              for (int r = 0; r < 4; ++r) el[r] += __shfl_xor_sync(0xFFFFFFFFu, el[r], o);
+          if ((tid & 31) < G || G >= 32)
 #pragma unroll
             for (int r = 0; r < 4; ++r)
-              if (4 * gi + r < T) atomicAdd(&eacc[4 * gi + r], (unsigned long long)(-(long long)sv[r] * h[r]));
-          }
+              if (4 * gfix + r < T && el[r]) atomicAdd(&eacc[4 * gfix + r], (unsigned long long)el[r]);
         }
         __syncthreads();
       }

@@ -422,15 +422,6 @@ __global__ void __launch_bounds__(QM_NT) k_qmodes_packed(Job jb, Dev dv, int Lma
 // P = (sites in the plane) - 2 (disagreements).
 constexpr int QW_NT = 256;
 
-// r / d for 0 <= r < 2^26 by a multiply-high with m = ceil((2^32 - 1) / d) (an estimate
-// off by at most one) and one correction each way.
-__device__ __forceinline__ int div_by(int r, int d, uint32_t m) {
-  int q = (int)__umulhi((uint32_t)r, m);
-  q += (q + 1) * d <= r ? 1 : 0;
-  q -= q * d > r ? 1 : 0;
-  return q;
-}
-
 // Empty a lane's bit-sliced x-plane counters into its pair's accumulators: bit t counts
 // the site of lane t (x = t mod L0 for rows of at most 32 sites, else 32 chunk + t).
 // The planes in use (those below the warp's highest nonzero one) are summed per x
@@ -515,7 +506,7 @@ __global__ void __launch_bounds__(QW_NT, 4) k_qmodes_w1(Job jb, Dev dv, int Lmax
   const int jrow = narrow ? lane / L0 : 0;
   const int x = narrow ? lane - jrow * L0 : 32 * chunk + lane;
   const bool lane_ok = narrow ? jrow < rps : x < L0;
-  const uint32_t mL1 = (uint32_t)((0xFFFFFFFFull + L1) / (unsigned)L1);
+  const uint32_t mL1 = div_magic(L1);
   uint32_t V[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) V[b] = 0u;

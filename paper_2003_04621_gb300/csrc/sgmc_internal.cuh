@@ -294,6 +294,20 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
   return x;
 }
 
+// r / d (d >= 1) for 0 <= r < 2^26 by a multiply-high with m = ceil((2^32 - 1) / d) (an estimate
+// off by at most one) and one correction each way.
+// div_magic(d) gives m.
+__device__ __forceinline__ int div_by(int r, int d, uint32_t m) {
+  int q = (int)__umulhi((uint32_t)r, m);
+  q += (q + 1) * d <= r ? 1 : 0;
+  q -= q * d > r ? 1 : 0;
+  return q;
+}
+__host__ __device__ inline uint32_t div_magic(int d) {
+  // d = 1: m = 2^32 - 1 gives r - 1 (r >= 1), which the upward correction makes r
+  return d <= 1 ? 0xFFFFFFFFu : (uint32_t)((0xFFFFFFFFull + (unsigned)d) / (unsigned)d);
+}
+
 // Byte-table permutation of a word: out = OR over bytes of tab[byte index][byte value].
 __device__ __forceinline__ uint32_t permute_word(const uint32_t *tab, uint32_t w) {
   return tab[w & 255u] | tab[256 + ((w >> 8) & 255u)] | tab[512 + ((w >> 16) & 255u)] | tab[768 + (w >> 24)];
