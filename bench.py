@@ -247,7 +247,10 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
                       "groups in parallel"}
 
 
-def bench_extensions(stream, steps: int = 5):
+EXTENSIONS = ("houdayer", "gauss", "trips", "houdayer3d")
+
+
+def bench_extensions(stream, steps: int = 5, only=None):
     """The rows beyond the core path, each timed with CUDA events on its own stream:
     the 2D L=128 Houdayer MCS with the single-cluster move and with the multi-cluster
     variant; the 2D L=16 Gaussian-coupling MCS; one overlap plane-sum measurement of the
@@ -269,8 +272,9 @@ def bench_extensions(stream, steps: int = 5):
         return a.elapsed_time(e) / n
 
     out = {}
+    want = set(only or EXTENSIONS)
     h = workload_2d_l128_houdayer()
-    for mode, name in ((True, "houdayer_single"), (2, "houdayer_multicluster")):
+    for mode, name in ((True, "houdayer_single"), (2, "houdayer_multicluster")) if "houdayer" in want else ():
         sim = Simulation(2, h.dims, h.n_samples, 2, list(h.temps), houdayer=mode, stream=stream)
         sim.set_launch(512, 2)
         ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
@@ -281,15 +285,17 @@ def bench_extensions(stream, steps: int = 5):
     from paper_2003_04621_gb300.inputs import gaussian_couplings_fixed, workload_2d_gauss_l16
 
     gw = workload_2d_gauss_l16()
-    sim = Simulation(2, gw.dims, gw.n_samples, 2, list(gw.temps), spin_format="int8", couplings="fixed",
-                     stream=stream)
-    sim.set_couplings_fixed(gaussian_couplings_fixed(gw.n_samples, gw.dims, seed=gw.coupling_seed), stream=stream)
-    ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
-    out["gauss_2d_l16"] = {"ms_per_mcs": ms, "attempts_per_ns": gw.attempts_per_sweep / (ms * 1e6),
-                           "workload": gw.name}
-    sim.close()
+    if "gauss" in want:
+        sim = Simulation(2, gw.dims, gw.n_samples, 2, list(gw.temps), spin_format="int8", couplings="fixed",
+                         stream=stream)
+        sim.set_couplings_fixed(gaussian_couplings_fixed(gw.n_samples, gw.dims, seed=gw.coupling_seed),
+                                stream=stream)
+        ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+        out["gauss_2d_l16"] = {"ms_per_mcs": ms, "attempts_per_ns": gw.attempts_per_sweep / (ms * 1e6),
+                               "workload": gw.name}
+        sim.close()
     u = workload_3d_l16()
-    for track in (False, True):
+    for track in (False, True) if "trips" in want else ():
         sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), track_trips=track, stream=stream)
         sim.set_launch(256, 2)
         ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
@@ -305,12 +311,13 @@ def bench_extensions(stream, steps: int = 5):
             out["qmodes_l16"] = {"ms_per_measurement": qms, "pairs": u.n_samples * u.T}
         sim.close()
     # the 3D L=16 job with the cluster move kept to its 8 lowest temperatures (0.9-1.1)
-    sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), houdayer=True, houdayer_slots=8, stream=stream)
-    sim.set_launch(256, 2)
-    ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
-    out["houdayer_3d_l16_low8"] = {"ms_per_mcs": ms, "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6),
-                                   "workload": u.name + "_houdayer_slots8"}
-    sim.close()
+    if "houdayer3d" in want:
+        sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), houdayer=True, houdayer_slots=8, stream=stream)
+        sim.set_launch(256, 2)
+        ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+        out["houdayer_3d_l16_low8"] = {"ms_per_mcs": ms, "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6),
+                                       "workload": u.name + "_houdayer_slots8"}
+        sim.close()
     return out
 
 
@@ -343,6 +350,8 @@ def main():
     ap.add_argument("--workload", default="3d_l16", choices=["3d_l16", "2d_l128_houdayer"],
                     help="3d_l16: the headline job; 2d_l128_houdayer: Metropolis + Houdayer + exchange")
     ap.add_argument("--serve-jobs", type=int, default=20)
+    ap.add_argument("--extension", action="append", choices=EXTENSIONS,
+                    help="time only these extension rows (repeatable) and print them as one JSON line")
     args = ap.parse_args()
     from paper_2003_04621_gb300.shard import dist_env, max_over_ranks, weak_shard
 
@@ -365,6 +374,10 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
+    if args.extension:
+        print(json.dumps({"extensions": bench_extensions(torch.cuda.Stream(), steps=max(1, args.steps),
+                                                         only=args.extension)}))
+        return
     from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer
 
     base = workload_3d_l16() if args.workload == "3d_l16" else workload_2d_l128_houdayer()

@@ -49,6 +49,27 @@ __device__ __forceinline__ uint32_t gauss_threshold(float beta, int dE) {
   return __float2uint_rz(__fmul_rn(e, 4294967296.0f));
 }
 
+// The Metropolis decision r < gauss_threshold(beta, dE) for dE > 0, decided first against
+// the hardware exponential.  __expf's documented error is at most 2 + floor(1.16 |x|)
+// ulp, under 3.4e-6 relative on [-23, 0]; gauss_exp is within 2e-6 of exp (a pinned
+// bound); fp32 r and the products add about 2e-7.  So for r below e_a 2^32 (1 - 2^-14) or
+// above e_a 2^32 (1 + 2^-14), e_a = __expf(x), the exact threshold gives the same answer
+// with a margin above ten times the error.  Only draws inside that band (a fraction of
+// about 1e-4) evaluate gauss_threshold.  Below x = -23 the exact threshold is 0: no draw
+// is accepted.
+// Returns 1 (accept: dE <= 0, or r clearly below), -1 (reject) or 0 (r inside the band:
+// the caller evaluates r < gauss_threshold(beta, dE)).
+__device__ __forceinline__ int gauss_fast(float beta, int dE, uint32_t r) {
+  const float xs = __fmul_rn(__int2float_rn(dE), 0x1p-20f);
+  const float x = -__fmul_rn(beta, xs);
+  const float ea = __fmul_rn(__expf(x), 4294967296.0f);
+  const float rf = __uint2float_rn(r);
+  const bool dead = x < -23.0f; // the exact threshold is 0 there
+  const bool lo = !dead && rf < __fmul_rn(ea, 1.0f - 0x1p-14f);
+  const bool hi = dead || rf > __fmul_rn(ea, 1.0f + 0x1p-14f);
+  return (dE <= 0 || lo) ? 1 : (hi ? -1 : 0);
+}
+
 __device__ __forceinline__ uint32_t word_of4(const uint4 &r, int i) {
   return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
 }
@@ -253,24 +274,28 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
           }
           int sv[4] = {s4.x, s4.y, s4.z, s4.w};
           if (!ENERGY_ONLY) {
-            int dE[4];
-            bool need = false;
+            const uint32_t i = (uint32_t)(g.L0 * sg.row + 2 * sg.k + sg.xodd);
+            const uint4 rnd =
+                philox10(i, t, s_glob, ((uint32_t)c << 20) | ((uint32_t)gi << 8) | TAG_METRO, jb.sk0, jb.sk1);
+            // decisions without branches; the rare draws near the threshold take the exact
+            // test afterwards
+            uint32_t acc = 0u, near = 0u;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-              dE[r] = 2 * sv[r] * h[r];
-              need |= (4 * gi + r < T) && dE[r] > 0;
+              const int dE = 2 * sv[r] * h[r];
+              const int f = gauss_fast(betaf[4 * gi + r], dE, word_of4(rnd, r));
+              acc |= (f > 0 ? 1u : 0u) << r;
+              near |= (f == 0 ? 1u : 0u) << r;
             }
-            uint4 rnd = make_uint4(0, 0, 0, 0);
-            if (need) {
-              const uint32_t i = (uint32_t)(g.L0 * sg.row + 2 * sg.k + sg.xodd);
-              rnd = philox10(i, t, s_glob, ((uint32_t)c << 20) | ((uint32_t)gi << 8) | TAG_METRO, jb.sk0,
-                             jb.sk1);
+            if (near) {
+#pragma unroll
+              for (int r = 0; r < 4; ++r)
+                if ((near >> r) & 1u)
+                  acc |= (word_of4(rnd, r) < gauss_threshold(betaf[4 * gi + r], 2 * sv[r] * h[r]) ? 1u : 0u) << r;
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int j = 4 * gi + r;
-              if (j < T && (dE[r] <= 0 || word_of4(rnd, r) < gauss_threshold(betaf[j], dE[r]))) sv[r] = -sv[r];
-            }
+            for (int r = 0; r < 4; ++r)
+              if (4 * gi + r < T && ((acc >> r) & 1u)) sv[r] = -sv[r];
             s4 = make_char4((signed char)sv[0], (signed char)sv[1], (signed char)sv[2], (signed char)sv[3]);
             *reinterpret_cast<char4 *>(sp8 + (size_t)p * Tp + 4 * gi) = s4;
           }
