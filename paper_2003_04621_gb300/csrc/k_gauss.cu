@@ -170,7 +170,7 @@ __device__ void exchange_chain64_warp(int T, const double *beta, int32_t *perm, 
   __syncwarp();
 }
 
-constexpr int GNT = 256;
+constexpr int GNT = 128;
 
 template <int D, bool FUSE_PT, bool ENERGY_ONLY>
 __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, int n_metro) {
