@@ -39,6 +39,20 @@ def phi_temps(t_min: float, t_max: float, n: int, phi: float) -> List[float]:
     return [math.pow(i, phi) * t_norm + t_min for i in range(n)]
 
 
+# The fitted optimum of the phi protocol for the 2D Gaussian EA model (Sec. 2.3, Eqs. 8-9):
+# phi*(L) = 0.406 + 0.014 L, N_T*(L) = 0.025 + 0.644 L, with T_min = 0.2 and T_max = 1.5.
+PHI_FIT = {"a_phi": 0.406, "b_phi": 0.014, "a_NT": 0.025, "b_NT": 0.644, "T_min": 0.2, "T_max": 1.5}
+
+
+def phi_protocol(L: int, n: int | None = None) -> List[float]:
+    """The phi-family set at the fitted optimum for linear size L (Eqs. 6-9): phi*(L),
+    and N_T*(L) rounded to the nearest integer (at least 2) unless n is given."""
+    phi = PHI_FIT["a_phi"] + PHI_FIT["b_phi"] * L
+    if n is None:
+        n = max(2, int(round(PHI_FIT["a_NT"] + PHI_FIT["b_NT"] * L)))
+    return phi_temps(PHI_FIT["T_min"], PHI_FIT["T_max"], n, phi)
+
+
 @dataclass
 class Workload:
     """One simulation job: the parameters the C-ABI's create call takes."""
@@ -152,5 +166,5 @@ def workload_2d_gauss_l16() -> Workload:
     with phi = 0.406 + 0.014 L (the fit of Eq. 8), int8 spins; couplings from
     gaussian_couplings_fixed(seed = coupling_seed)."""
     L = 16
-    return Workload("2d_L16_S512_T32_gauss", 2, (L, L), 512, 2, phi_temps(0.2, 1.5, 32, 0.406 + 0.014 * L),
-                    spin_format="int8", n_mcs=10000)
+    return Workload("2d_L16_S512_T32_gauss", 2, (L, L), 512, 2, phi_protocol(L, 32), spin_format="int8",
+                    n_mcs=10000)

@@ -134,3 +134,44 @@ def test_hot_start_is_balanced_and_keyed_by_sample(oracle_mod):
     np.testing.assert_array_equal(bits[2:], b.spins())
     np.testing.assert_array_equal(a.couplings()[2:], b.couplings())
     np.testing.assert_array_equal(a.energies()[2:], b.energies())
+
+
+def _golden(name):
+    import os
+
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+def test_phi_protocol_matches_the_printed_fit():
+    """Sec. 2.3: the phi family (Eqs. 6-7) at the fitted optimum of Eqs. 8-9, constants as
+    printed (tests/golden/phi_protocol_fit.txt)."""
+    from paper_2003_04621_gb300 import inputs
+
+    g = _golden("phi_protocol_fit.txt")
+    assert inputs.PHI_FIT == g
+    for L in (8, 15, 16, 40, 64):
+        T = inputs.phi_protocol(L)
+        phi = g["a_phi"] + g["b_phi"] * L
+        n = max(2, round(g["a_NT"] + g["b_NT"] * L))
+        assert len(T) == n
+        assert T[0] == g["T_min"] and abs(T[-1] - g["T_max"]) < 1e-12
+        steps = np.diff(T)
+        assert np.all(steps > 0)
+        # phi < 1 spaces the set more densely towards high temperatures, phi > 1 towards low
+        if phi < 1:
+            assert steps[-1] < steps[0]
+        elif phi > 1:
+            assert steps[-1] > steps[0]
+    # phi = 1 is the linear schedule
+    lin = inputs.phi_temps(0.2, 1.5, 11, 1.0)
+    assert np.allclose(lin, np.linspace(0.2, 1.5, 11), rtol=0, atol=1e-12)
+    # the 2D Gaussian job uses phi*(16) with 32 points
+    w = inputs.workload_2d_gauss_l16()
+    assert np.allclose(w.temps, inputs.phi_temps(0.2, 1.5, 32, 0.406 + 0.014 * 16), rtol=0, atol=0)
