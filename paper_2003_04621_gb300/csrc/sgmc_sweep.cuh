@@ -147,6 +147,36 @@ __device__ __forceinline__ uint4 philox_finish(const PhiloxSweep &P, const Philo
   return make_uint4(x0, x1, x2, x3);
 }
 
+// Two calls of philox_finish with counters (i, t, s, c3a) and (i, t, s, c3b), written
+// round by round so that the two independent chains interleave.
+__device__ __forceinline__ void philox_finish2(const PhiloxSweep &P, const PhiloxSite &Q, uint32_t c3a,
+                                               uint32_t c3b, const Job &jb, uint4 &ra, uint4 &rb) {
+  const uint32_t ya = Q.X ^ c3a, yb = Q.X ^ c3b;
+  uint32_t ha, la, hb, lb;
+  mulwide(PH_M1, ya, ha, la);
+  mulwide(PH_M1, yb, hb, lb);
+  const uint32_t z0a = ha ^ P.B ^ jb.rk0[1], z0b = hb ^ P.B ^ jb.rk0[1];
+  uint32_t pah, pal, pbh, pbl;
+  mulwide(PH_M0, z0a, pah, pal);
+  mulwide(PH_M0, z0b, pbh, pbl);
+  uint32_t a0 = Q.hiZ ^ la ^ jb.rk0[2], a1 = Q.loZ, a2 = pah ^ Q.z3 ^ jb.rk1[2], a3 = pal;
+  uint32_t b0 = Q.hiZ ^ lb ^ jb.rk0[2], b1 = Q.loZ, b2 = pbh ^ Q.z3 ^ jb.rk1[2], b3 = pbl;
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    uint32_t ah0, al0, ah1, al1, bh0, bl0, bh1, bl1;
+    mulwide(PH_M0, a0, ah0, al0);
+    mulwide(PH_M0, b0, bh0, bl0);
+    mulwide(PH_M1, a2, ah1, al1);
+    mulwide(PH_M1, b2, bh1, bl1);
+    const uint32_t na0 = ah1 ^ a1 ^ jb.rk0[r], na2 = ah0 ^ a3 ^ jb.rk1[r];
+    const uint32_t nb0 = bh1 ^ b1 ^ jb.rk0[r], nb2 = bh0 ^ b3 ^ jb.rk1[r];
+    a0 = na0; a1 = al1; a2 = na2; a3 = al0;
+    b0 = nb0; b1 = bl1; b2 = nb2; b3 = bl0;
+  }
+  ra = make_uint4(a0, a1, a2, a3);
+  rb = make_uint4(b0, b1, b2, b3);
+}
+
 // Bit-sliced unsatisfied-bond count of one site for 32 replicas: the adder planes.
 template <int D>
 struct SiteCount {
@@ -196,7 +226,31 @@ __device__ __forceinline__ void recount(const SiteCount<D> &c, uint32_t F, uint3
   }
 }
 
-// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.
+// The reject bits of one group of four lanes (4 gi .. 4 gi + 3) pushed onto rej, highest
+// lane first: their thresholds come from the lane-pair tables (see decide_site).
+template <int D>
+__device__ __forceinline__ uint32_t decide_group(uint32_t rej, const uint4 &r, int gi, const SiteCount<D> &cnt,
+                                                 const uint2 *__restrict__ pair_tab) {
+  uint2 th[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int pp = 2 * gi + h; // lanes 2pp, 2pp+1
+    // byte offset = 8 * code, code = (u0 >> 2pp) & 3 | ((u1 >> 2pp) & 3) << 2
+    const int s0 = 2 * pp - 3, s1 = 2 * pp - 5;
+    const uint32_t a0 = s0 >= 0 ? (cnt.u0 >> s0) : (cnt.u0 << (-s0));
+    const uint32_t a1 = s1 >= 0 ? (cnt.u1 >> s1) : (cnt.u1 << (-s1));
+    const uint32_t off = (a0 & 0x18u) | (a1 & 0x60u);
+    th[h] = *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(pair_tab) + pp * 128 + off);
+  }
+  rej = push_reject(rej, r.w, th[1].y);
+  rej = push_reject(rej, r.z, th[1].x);
+  rej = push_reject(rej, r.y, th[0].y);
+  rej = push_reject(rej, r.x, th[0].x);
+  return rej;
+}
+
+// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.  The
+// groups are taken two at a time (their Philox calls interleaved), highest first.
 // pair_tab holds, for each pair of lanes (2p, 2p+1) and each 4-bit code
 // (u0_2p, u0_2p+1, u1_2p, u1_2p+1), the two lanes' thresholds for their counts u
 // (m = d - u), 8 bytes per entry: one 64-bit load serves two lanes, and the code is
@@ -207,26 +261,19 @@ __device__ __forceinline__ uint32_t decide_site(const SiteCount<D> &cnt, const P
                                                 const uint2 *__restrict__ pair_tab, const Job &jb) {
   uint32_t rej = 0;
 #pragma unroll
-  for (int gi = 7; gi >= 0; --gi) {
-    if (gi < ngroups) {
-      const uint4 r = philox_finish(P, Q, c3base | ((uint32_t)gi << 8), jb);
-      uint2 th[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int pp = 2 * gi + h; // lanes 2pp, 2pp+1
-        // byte offset = 8 * code, code = (u0 >> 2pp) & 3 | ((u1 >> 2pp) & 3) << 2
-        const int s0 = 2 * pp - 3, s1 = 2 * pp - 5;
-        const uint32_t a0 = s0 >= 0 ? (cnt.u0 >> s0) : (cnt.u0 << (-s0));
-        const uint32_t a1 = s1 >= 0 ? (cnt.u1 >> s1) : (cnt.u1 << (-s1));
-        const uint32_t off = (a0 & 0x18u) | (a1 & 0x60u);
-        th[h] = *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(pair_tab) + pp * 128 + off);
-      }
-      rej = push_reject(rej, r.w, th[1].y);
-      rej = push_reject(rej, r.z, th[1].x);
-      rej = push_reject(rej, r.y, th[0].y);
-      rej = push_reject(rej, r.x, th[0].x);
+  for (int gp = 3; gp >= 0; --gp) {
+    const int ga = 2 * gp + 1, gb = 2 * gp;
+    if (ga < ngroups) {
+      uint4 ra, rb;
+      philox_finish2(P, Q, c3base | ((uint32_t)ga << 8), c3base | ((uint32_t)gb << 8), jb, ra, rb);
+      rej = decide_group<D>(rej, ra, ga, cnt, pair_tab);
+      rej = decide_group<D>(rej, rb, gb, cnt, pair_tab);
+    } else if (gb < ngroups) {
+      rej <<= 4;
+      const uint4 rb = philox_finish(P, Q, c3base | ((uint32_t)gb << 8), jb);
+      rej = decide_group<D>(rej, rb, gb, cnt, pair_tab);
     } else {
-      rej <<= 4; // lanes past the last group: not decided here
+      rej <<= 8;
     }
   }
   return cnt.aut | ~rej;
