@@ -147,34 +147,38 @@ __device__ __forceinline__ uint4 philox_finish(const PhiloxSweep &P, const Philo
   return make_uint4(x0, x1, x2, x3);
 }
 
-// Two calls of philox_finish with counters (i, t, s, c3a) and (i, t, s, c3b), written
-// round by round so that the two independent chains interleave.
-__device__ __forceinline__ void philox_finish2(const PhiloxSweep &P, const PhiloxSite &Q, uint32_t c3a,
-                                               uint32_t c3b, const Job &jb, uint4 &ra, uint4 &rb) {
-  const uint32_t ya = Q.X ^ c3a, yb = Q.X ^ c3b;
-  uint32_t ha, la, hb, lb;
-  mulwide(PH_M1, ya, ha, la);
-  mulwide(PH_M1, yb, hb, lb);
-  const uint32_t z0a = ha ^ P.B ^ jb.rk0[1], z0b = hb ^ P.B ^ jb.rk0[1];
-  uint32_t pah, pal, pbh, pbl;
-  mulwide(PH_M0, z0a, pah, pal);
-  mulwide(PH_M0, z0b, pbh, pbl);
-  uint32_t a0 = Q.hiZ ^ la ^ jb.rk0[2], a1 = Q.loZ, a2 = pah ^ Q.z3 ^ jb.rk1[2], a3 = pal;
-  uint32_t b0 = Q.hiZ ^ lb ^ jb.rk0[2], b1 = Q.loZ, b2 = pbh ^ Q.z3 ^ jb.rk1[2], b3 = pbl;
+// K calls of philox_finish for the groups g0 .. g0 + K - 1 (counters (i, t, s,
+// c3base | g << 8)), written round by round so that the K independent chains interleave.
+template <int K>
+__device__ __forceinline__ void philox_finishK(const PhiloxSweep &P, const PhiloxSite &Q, uint32_t c3base, int g0,
+                                               const Job &jb, uint4 (&out)[K]) {
+  uint32_t a0[K], a1[K], a2[K], a3[K];
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const uint32_t y = Q.X ^ (c3base | ((uint32_t)(g0 + u) << 8));
+    uint32_t h, l;
+    mulwide(PH_M1, y, h, l);
+    const uint32_t z0 = h ^ P.B ^ jb.rk0[1];
+    uint32_t ph, pl;
+    mulwide(PH_M0, z0, ph, pl);
+    a0[u] = Q.hiZ ^ l ^ jb.rk0[2];
+    a1[u] = Q.loZ;
+    a2[u] = ph ^ Q.z3 ^ jb.rk1[2];
+    a3[u] = pl;
+  }
 #pragma unroll
   for (int r = 3; r < 10; ++r) {
-    uint32_t ah0, al0, ah1, al1, bh0, bl0, bh1, bl1;
-    mulwide(PH_M0, a0, ah0, al0);
-    mulwide(PH_M0, b0, bh0, bl0);
-    mulwide(PH_M1, a2, ah1, al1);
-    mulwide(PH_M1, b2, bh1, bl1);
-    const uint32_t na0 = ah1 ^ a1 ^ jb.rk0[r], na2 = ah0 ^ a3 ^ jb.rk1[r];
-    const uint32_t nb0 = bh1 ^ b1 ^ jb.rk0[r], nb2 = bh0 ^ b3 ^ jb.rk1[r];
-    a0 = na0; a1 = al1; a2 = na2; a3 = al0;
-    b0 = nb0; b1 = bl1; b2 = nb2; b3 = bl0;
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      uint32_t h0, l0, h1, l1;
+      mulwide(PH_M0, a0[u], h0, l0);
+      mulwide(PH_M1, a2[u], h1, l1);
+      const uint32_t n0 = h1 ^ a1[u] ^ jb.rk0[r], n2 = h0 ^ a3[u] ^ jb.rk1[r];
+      a0[u] = n0; a1[u] = l1; a2[u] = n2; a3[u] = l0;
+    }
   }
-  ra = make_uint4(a0, a1, a2, a3);
-  rb = make_uint4(b0, b1, b2, b3);
+#pragma unroll
+  for (int u = 0; u < K; ++u) out[u] = make_uint4(a0[u], a1[u], a2[u], a3[u]);
 }
 
 // Bit-sliced unsatisfied-bond count of one site for 32 replicas: the adder planes.
@@ -249,8 +253,9 @@ __device__ __forceinline__ uint32_t decide_group(uint32_t rej, const uint4 &r, i
   return rej;
 }
 
-// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.  The
-// groups are taken two at a time (their Philox calls interleaved), highest first.
+// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.  A full
+// word's eight groups draw their words in one interleaved Philox evaluation, a partial
+// word's two at a time; the reject bits are pushed highest group first.
 // pair_tab holds, for each pair of lanes (2p, 2p+1) and each 4-bit code
 // (u0_2p, u0_2p+1, u1_2p, u1_2p+1), the two lanes' thresholds for their counts u
 // (m = d - u), 8 bytes per entry: one 64-bit load serves two lanes, and the code is
@@ -260,14 +265,21 @@ __device__ __forceinline__ uint32_t decide_site(const SiteCount<D> &cnt, const P
                                                 const PhiloxSite &Q, uint32_t c3base, int ngroups,
                                                 const uint2 *__restrict__ pair_tab, const Job &jb) {
   uint32_t rej = 0;
+  if (ngroups == 8) { // a full word: all eight groups in one interleaved evaluation
+    uint4 rr[8];
+    philox_finishK<8>(P, Q, c3base, 0, jb, rr);
+#pragma unroll
+    for (int u = 7; u >= 0; --u) rej = decide_group<D>(rej, rr[u], u, cnt, pair_tab);
+    return cnt.aut | ~rej;
+  }
 #pragma unroll
   for (int gp = 3; gp >= 0; --gp) {
     const int ga = 2 * gp + 1, gb = 2 * gp;
     if (ga < ngroups) {
-      uint4 ra, rb;
-      philox_finish2(P, Q, c3base | ((uint32_t)ga << 8), c3base | ((uint32_t)gb << 8), jb, ra, rb);
-      rej = decide_group<D>(rej, ra, ga, cnt, pair_tab);
-      rej = decide_group<D>(rej, rb, gb, cnt, pair_tab);
+      uint4 rr[2];
+      philox_finishK<2>(P, Q, c3base, gb, jb, rr);
+      rej = decide_group<D>(rej, rr[1], ga, cnt, pair_tab);
+      rej = decide_group<D>(rej, rr[0], gb, cnt, pair_tab);
     } else if (gb < ngroups) {
       rej <<= 4;
       const uint4 rb = philox_finish(P, Q, c3base | ((uint32_t)gb << 8), jb);
