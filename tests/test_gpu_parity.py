@@ -283,3 +283,32 @@ def test_every_launch_shape_gives_identical_results(oracle_mod, ndim, dims, T):
             assert_same_state(sim, orc, f"threads={nt} words={words}")
             ran += 1
     assert ran >= 2
+
+
+@pytest.mark.parametrize("fmt", ["packed", "int8"])
+def test_maximum_temperature_count(oracle_mod, fmt):
+    """n_temps at its limit, 4096: a chain of 128 words (packed) or 4096 bytes per site
+    (int8) on a 4x4 lattice; sweeps, exchange passes and the measurement at that size."""
+    kw = dict(ndim=2, dims=(4, 4), n_samples=1, n_chains=2, temps=geometric_temps(0.3, 5.0, 4096), sim_seed=13,
+              coupling_seed=2, spin_format=fmt)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_oracle_kw(kw))
+    for t in range(3):
+        sim.run_mcs(1)
+        orc.mcs(1)
+        assert_same_state(sim, orc, f"mcs {t}")
+
+
+def test_maximum_lattice(oracle_mod):
+    """N at its limit, 2^26 sites (2D 8192 x 8192), one chain of one replica; 2^26 + 2
+    more sites are refused (the create call's checks run on the host)."""
+    from paper_2003_04621_gb300.sgmc import SGError
+
+    kw = dict(ndim=2, dims=(8192, 8192), n_samples=1, n_chains=1, temps=[2.2], sim_seed=17, coupling_seed=19)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_oracle_kw(kw))
+    sim.run_mcs(1)
+    orc.mcs(1)
+    assert_same_state(sim, orc, "mcs 1")
+    sim.close()
+    with pytest.raises(SGError) as e:
+        gpu_of(**dict(kw, dims=(8192, 8194)))
+    assert e.value.status == 5
