@@ -30,22 +30,27 @@ __global__ void k_init_couplings(Job jb, Dev dv) {
 // Hot start, packed: thread per (sample, word, site).
 __global__ void k_init_spins_packed(Job jb, Dev dv) {
   const Geo g = jb.g;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)jb.S * jb.W * g.N) return;
-  const int p = (int)(idx % g.N);
-  const int w = (int)((idx / g.N) % jb.W);
-  const int s = (int)(idx / ((long long)g.N * jb.W));
-  const int c = w / jb.Wc, wc = w - c * jb.Wc;
-  const int nvalid = min(32, jb.T - wc * 32);
+  const int p = blockIdx.x * blockDim.x + threadIdx.x; // site (colour-split order)
+  if (p >= g.N) return;
   const uint32_t i = (uint32_t)canonical_of(g, site_geo(g, p));
-  uint32_t word = 0;
-  for (int gi = 0; gi * 4 < nvalid; ++gi) {
-    const uint32_t c3 = ((uint32_t)c << 20) | ((uint32_t)(wc * 8 + gi) << 8) | TAG_INIT;
-    const uint4 r = philox10(i, 0u, (uint32_t)(jb.s_off + s), c3, jb.sk0, jb.sk1);
-    for (int q = 0; q < 4; ++q)
-      if (gi * 4 + q < nvalid) word |= (word_of(r, q) >> 31) << (gi * 4 + q);
+  for (int plane = blockIdx.y; plane < jb.S * jb.W; plane += gridDim.y) { // (sample, word)
+    const int s = plane / jb.W, w = plane - s * jb.W;
+    const int c = w / jb.Wc, wc = w - c * jb.Wc;
+    const int nvalid = min(32, jb.T - wc * 32);
+    // the word's eight calls are independent: evaluate them together, keep the valid lanes
+    uint4 r[8];
+#pragma unroll
+    for (int gi = 0; gi < 8; ++gi) {
+      const uint32_t c3 = ((uint32_t)c << 20) | ((uint32_t)(wc * 8 + gi) << 8) | TAG_INIT;
+      r[gi] = philox10(i, 0u, (uint32_t)(jb.s_off + s), c3, jb.sk0, jb.sk1);
+    }
+    uint32_t word = 0;
+#pragma unroll
+    for (int gi = 0; gi < 8; ++gi)
+      word |= ((r[gi].x >> 31) | ((r[gi].y >> 31) << 1) | ((r[gi].z >> 31) << 2) | ((r[gi].w >> 31) << 3)) << (4 * gi);
+    if (nvalid < 32) word &= (1u << nvalid) - 1u;
+    dv.spins[(size_t)plane * g.N + p] = word;
   }
-  dv.spins[idx] = word;
 }
 
 // Hot start, int8: thread per (sample, chain, site, group of four replicas).
@@ -686,8 +691,8 @@ cudaError_t launch_init(const Job &jb, const Dev &dv, bool int8fmt, cudaStream_t
     const long long n = (long long)jb.S * jb.C * jb.g.N * (jb.Tp / 4);
     k_init_spins_int8<<<blocks_for(n, 128), 128, 0, st>>>(jb, dv);
   } else {
-    const long long n = (long long)jb.S * jb.W * jb.g.N;
-    k_init_spins_packed<<<blocks_for(n, 128), 128, 0, st>>>(jb, dv);
+    const unsigned planes = (unsigned)min(jb.S * jb.W, 65535);
+    k_init_spins_packed<<<dim3((unsigned)((jb.g.N + 127) / 128), planes), 128, 0, st>>>(jb, dv);
   }
   k_init_maps<<<blocks_for((long long)jb.S * jb.C * jb.T, 256), 256, 0, st>>>(jb, dv);
   return cudaGetLastError();
