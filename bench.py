@@ -321,20 +321,30 @@ def bench_extensions(stream, steps: int = 5, only=None):
     return out
 
 
-def bench_serving(n_jobs: int, rate: float = 50.0):
-    """Poisson(50/s, seed 7) stream of jobs served by continuous batching; p50/p99 latency."""
+def bench_serving(n_jobs: int, rate: float = 50.0, below=(2.0, 10)):
+    """Poisson(50/s, seed 7) stream of jobs served by continuous batching; p50/p99 latency.
+    `below` = (rate, jobs) repeats it at a rate under the GPU's capacity, where latency is
+    the jobs' own run time rather than time in the queue."""
     import torch
 
     from paper_2003_04621_gb300.serve import Server, poisson_trace, summarize
 
     free, _total = torch.cuda.mem_get_info()
     arena = int(min(32 << 30, free // 3))
-    server = Server(arena_bytes=arena, quantum=100)
-    results = server.run(poisson_trace(n_jobs, rate=rate, seed=7))
-    out = summarize(results)
-    out.update({"rate_per_s": rate, "arena_gb": arena / 2**30, "quantum_mcs": 100,
-                "graph_builds": server.graph_builds, "graph_launches": server.graph_launches,
-                "trace": f"first {n_jobs} arrivals of the Poisson({rate}/s, seed 7) stream"})
+
+    def serve(n, r):
+        server = Server(arena_bytes=arena, quantum=100)
+        res = summarize(server.run(poisson_trace(n, rate=r, seed=7)))
+        res.update({"rate_per_s": r, "graph_builds": server.graph_builds, "graph_launches": server.graph_launches,
+                    "trace": f"first {n} arrivals of the Poisson({r}/s, seed 7) stream"})
+        del server
+        torch.cuda.synchronize()
+        return res
+
+    out = serve(n_jobs, rate)
+    out.update({"arena_gb": arena / 2**30, "quantum_mcs": 100})
+    if below:
+        out["below_saturation"] = serve(int(below[1]), float(below[0]))
     return out
 
 
