@@ -151,14 +151,21 @@ sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t str
 /* As sg_measure, into DEVICE buffers of the same shapes, without synchronising. */
 sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
 
-/* As sg_measure into HOST buffers, but only enqueued on `stream`: the kernel and the two
- * device-to-host copies run when the stream reaches them, so the host can queue the
- * next steps at once.  The caller keeps the buffers alive and unread until it has
- * synchronised the stream; page-locked (pinned) buffers let the copies run without
- * blocking the host.  Later calls reuse the handle's device staging area in stream
- * order, so each call may target its own host buffers.  A device-side error (a bulk-
- * copy wait that ran out) is reported by the next call that synchronises. */
+/* As sg_measure into HOST buffers, but only enqueued: the measurement kernel runs on
+ * `stream` when it gets there, and the two device-to-host copies then run on a copy
+ * stream owned by the handle, so `stream` goes on with its next work (the next MCS)
+ * while they run.  Two staging slots alternate; a slot is rewritten only after its
+ * previous copies have finished.  The values are in the host buffers once
+ * sg_measure_wait(h) has returned (or the device has been synchronised); the caller
+ * keeps the buffers alive and unread until then.  Page-locked (pinned) buffers let the
+ * copies run without blocking the host.  While `stream` is being captured into a CUDA
+ * graph the copies stay on `stream` (no second stream enters the capture).  A
+ * device-side error (a bulk-copy wait that ran out) is reported by the next call that
+ * synchronises. */
 sg_status sg_measure_async(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
+
+/* Wait for every copy that sg_measure_async has enqueued on the handle's copy stream. */
+sg_status sg_measure_wait(sg_handle *h);
 
 /* Round trips in temperature (Sec. 2.3: lowest -> highest -> lowest), counted after
  * every exchange pass t = 1, 2, ...: a replica at the lowest slot whose last extreme was

@@ -45,6 +45,20 @@ struct sg_handle {
   bool global;     // sweeps stream the lattice from global memory (no resident kernel)
   bool gauss;      // general fixed-point couplings (k_gauss.cu)
   int n_ctr;       // counters in the device array
+  // sg_measure_async: device-to-host copies on a copy stream of the handle, from two
+  // alternating staging slots (created at the first asynchronous measurement)
+  cudaStream_t cst = nullptr;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr}; // slot's observables written (caller's stream)
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};  // slot's copies finished (copy stream)
+  bool slot_used[2] = {false, false};
+  int mslot = 0;
+  ~sg_handle() {
+    if (cst) cudaStreamDestroy(cst);
+    for (int i = 0; i < 2; ++i) {
+      if (ev_ready[i]) cudaEventDestroy(ev_ready[i]);
+      if (ev_done[i]) cudaEventDestroy(ev_done[i]);
+    }
+  }
 };
 
 namespace {
@@ -138,8 +152,8 @@ Layout layout_of(const sg_params *p, const Job &jb) {
   L.thr = take(T * 4 * 4);
   L.beta = take(T * 8);
   L.ctr = take((size_t)(CTR_PT + T) * 8);
-  L.meas_E = take(S * C * T * 4);
-  L.meas_Q = take(S * T * 4);
+  L.meas_E = take(2 * S * C * T * 4); // two staging slots (asynchronous measurements)
+  L.meas_Q = take(2 * S * T * 4);
   L.meas_P = take(C >= 2 ? S * T * (size_t)g.d * (size_t)qmodes_lmax(jb) * 4 : 0);
   // streaming sweep path: lane-pair threshold tables and per-replica bond sums
   L.gtab = take(S * (size_t)jb.W * 256 * 8);
@@ -307,6 +321,56 @@ sg_status poll_device_error(sg_handle *h, cudaStream_t st) {
   return SG_OK;
 }
 
+} // namespace
+
+namespace {
+// The copy stream and events of asynchronous measurements, created once per handle.
+cudaError_t ensure_copy_stream(sg_handle *h) {
+  if (h->cst) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_ready[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming);
+  }
+  return e;
+}
+
+// E by slot and N q into host buffers.  `side`: copy on the handle's copy stream from
+// alternating staging slots, so that `st` goes on with its next work while the copies
+// run (not while `st` is being captured into a graph); otherwise copy on `st` from slot 0.
+sg_status measure_to_host(sg_handle *h, int32_t *E_out, int32_t *Q_out, cudaStream_t st, bool side) {
+  if (!h || !E_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->gauss) return SG_EUNSUPPORTED;
+  if (side) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) side = false;
+  }
+  if (side && ensure_copy_stream(h) != cudaSuccess) side = false;
+  const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
+  const int slot = side ? h->mslot : 0;
+  if (side) h->mslot ^= 1;
+  int32_t *dE = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_E) + slot * nE;
+  int32_t *dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q) + slot * nQ;
+  const bool want_q = Q_out && h->job.C >= 2;
+  cudaError_t e = cudaSuccess;
+  // the slot is rewritten only after its previous copies have finished
+  if (side && h->slot_used[slot]) e = cudaStreamWaitEvent(st, h->ev_done[slot], 0);
+  if (e == cudaSuccess) e = launch_measure(h->job, h->dev, h->int8fmt != 0, dE, want_q ? dQ : nullptr, st);
+  cudaStream_t cp = st;
+  if (side) {
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_ready[slot], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cst, h->ev_ready[slot], 0);
+    cp = h->cst;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, cp);
+  if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, cp);
+  if (side && e == cudaSuccess) {
+    e = cudaEventRecord(h->ev_done[slot], h->cst);
+    h->slot_used[slot] = true;
+  }
+  return check(h, e);
+}
 } // namespace
 
 extern "C" {
@@ -705,23 +769,18 @@ sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintpt
 }
 
 sg_status sg_measure_async(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
-  if (!h || !E_out) return SG_EINVAL;
+  return measure_to_host(h, E_out, Q_out, as_stream(stream), true);
+}
+
+sg_status sg_measure_wait(sg_handle *h) {
+  if (!h) return SG_EINVAL;
   if (h->sticky != SG_OK) return h->sticky;
-  if (h->gauss) return SG_EUNSUPPORTED;
-  cudaStream_t st = as_stream(stream);
-  int32_t *dE = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_E);
-  int32_t *dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q);
-  const bool want_q = Q_out && h->job.C >= 2;
-  sg_status r = sg_measure_device(h, dE, want_q ? dQ : nullptr, stream);
-  if (r != SG_OK) return r;
-  const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
-  cudaError_t e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, st);
-  return check(h, e);
+  if (!h->cst) return SG_OK;
+  return check(h, cudaStreamSynchronize(h->cst));
 }
 
 sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
-  const sg_status r = sg_measure_async(h, E_out, Q_out, stream);
+  const sg_status r = measure_to_host(h, E_out, Q_out, as_stream(stream), false);
   if (r != SG_OK) return r;
   return poll_device_error(h, as_stream(stream));
 }

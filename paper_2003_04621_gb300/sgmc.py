@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
 
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
-    "sg_measure", "sg_measure_device", "sg_measure_async", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
+    "sg_measure", "sg_measure_device", "sg_measure_async", "sg_measure_wait", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
     "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_checkpoint_bytes", "sg_checkpoint",
     "sg_restore", "sg_selftest_wait", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
@@ -84,6 +84,7 @@ def lib():
         "sg_measure": [P, P, P, U],
         "sg_measure_device": [P, P, P, U],
         "sg_measure_async": [P, P, P, U],
+        "sg_measure_wait": [P],
         "sg_measure_qmodes": [P, P, U],
         "sg_trips": [P, P, P, U],
         "sg_measure_qmodes_device": [P, P, U],
@@ -277,8 +278,8 @@ class Simulation:
 
     def measure_async(self, E, Q=None, stream=None):
         """As measure(out=(E, Q)) but only enqueued: the arrays (C-contiguous int32 of the
-        measure shapes, ideally views of pinned tensors) hold the values once the stream
-        has been synchronised.  Keep them alive until then."""
+        measure shapes, ideally views of pinned tensors) hold the values once measure_wait()
+        has returned or the device has been synchronised.  Keep them alive until then."""
         if self.gauss:
             raise SGError(5, "sg_measure_async")
         if E.dtype != np.int32 or E.shape != (self.S, self.C, self.T) or not E.flags.c_contiguous:
@@ -287,6 +288,10 @@ class Simulation:
             raise ValueError("Q must be a C-contiguous int32 array of shape [S][T]")
         _check(lib().sg_measure_async(self._h, E.ctypes.data, Q.ctypes.data if Q is not None else None,
                                       self._s(stream)), "sg_measure_async")
+
+    def measure_wait(self):
+        """Wait for the copies of every measure_async call on this simulation."""
+        _check(lib().sg_measure_wait(self._h), "sg_measure_wait")
 
     def measure_device(self, E_out, Q_out=None, stream=None):
         """As measure, into torch int32 device tensors; does not synchronise."""

@@ -85,8 +85,9 @@ def test_single_pass_measurement_large_lattices(oracle_mod, ndim, dims, T):
 
 def test_asynchronous_measurement_ring(oracle_mod):
     """sg_measure_async: one read per MCS into its own slot of a pinned ring, queued
-    behind the MCS without synchronising; every slot equals the oracle's measurement
-    after the same number of MCS."""
+    behind the MCS without synchronising (the copies on the simulation's copy stream,
+    from alternating staging slots); after sg_measure_wait every slot equals the oracle's
+    measurement after the same number of MCS, and a synchronous read afterwards agrees."""
     import torch
 
     kw = dict(ndim=3, dims=(8, 8, 8), n_samples=3, n_chains=2, temps=geometric_temps(0.5, 2.0, 12), sim_seed=41)
@@ -97,12 +98,15 @@ def test_asynchronous_measurement_ring(oracle_mod):
     for k in range(n):
         sim.run_mcs(1)
         sim.measure_async(E[k], Q[k])
-    torch.cuda.synchronize()
+    sim.measure_wait()  # the copies, on the simulation's copy stream, are done
     for k in range(n):
         orc.mcs(1)
         E_o, Q_o = orc.measure()
         np.testing.assert_array_equal(E[k], E_o, err_msg=f"E slot {k}")
         np.testing.assert_array_equal(Q[k], Q_o, err_msg=f"N q slot {k}")
+    E_s, Q_s = sim.measure()
+    np.testing.assert_array_equal(E_s, E[-1])
+    np.testing.assert_array_equal(Q_s, Q[-1])
 
 
 
