@@ -164,7 +164,8 @@ sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintpt
  * synchronises. */
 sg_status sg_measure_async(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
 
-/* Wait for every copy that sg_measure_async has enqueued on the handle's copy stream. */
+/* Wait for every copy that sg_measure_async has enqueued on the handle's copy stream.
+ * sg_restore and sg_destroy wait for them too before they touch or release anything. */
 sg_status sg_measure_wait(sg_handle *h);
 
 /* Round trips in temperature (Sec. 2.3: lowest -> highest -> lowest), counted after

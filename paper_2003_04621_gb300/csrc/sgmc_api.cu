@@ -53,7 +53,10 @@ struct sg_handle {
   bool slot_used[2] = {false, false};
   int mslot = 0;
   ~sg_handle() {
-    if (cst) cudaStreamDestroy(cst);
+    if (cst) { // copies still in flight read the caller's buffer: let them finish first
+      cudaStreamSynchronize(cst);
+      cudaStreamDestroy(cst);
+    }
     for (int i = 0; i < 2; ++i) {
       if (ev_ready[i]) cudaEventDestroy(ev_ready[i]);
       if (ev_done[i]) cudaEventDestroy(ev_done[i]);
@@ -1070,6 +1073,10 @@ sg_status sg_restore(sg_handle *h, const void *host_in, size_t bytes, uintptr_t 
   if (h->sticky != SG_OK) return h->sticky;
   if (bytes < ckpt_bytes(h)) return SG_EINVAL;
   const char *in = static_cast<const char *>(host_in);
+  if (h->cst) { // asynchronous measurements still copying from the staging slots
+    const cudaError_t w = cudaStreamSynchronize(h->cst);
+    if (w != cudaSuccess) return check(h, w);
+  }
   CkptHeader c, mine = header_of(h);
   memcpy(&c, in, sizeof(c));
   // everything but the step counters must match this handle
