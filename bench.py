@@ -454,8 +454,7 @@ def main():
         sim2 = Simulation(stream=stream, **kw)
         sim2.set_launch(launch["threads"], launch["words"])
         for k in range(args.steps):
-            sim2.run_mcs(1, stream=stream)
-            sim2.measure_async(E[k], Q[k], stream=stream)
+            sim2.run_mcs_measure_async(1, E[k], Q[k], stream=stream)
         sim2.measure_wait()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
@@ -467,8 +466,9 @@ def main():
         e2e = {"value": attempts_per_step * args.steps / (e2e_s * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "includes": "create (H2D tables, device init) + per step one MCS and a D2H read of E and q "
-                           "into a pinned per-step ring (measurement kernel behind the MCS, copies on the "
-                           "simulation's copy stream overlapping the next MCS); timed until all have landed"}
+                           "into a pinned per-step ring (the measurement inside the MCS launch where the kernel "
+                           "holds both chains, copies on the simulation's copy stream overlapping the next MCS); "
+                           "timed until all have landed"}
         sim2.close()
 
     pk, pk_kind = peaks()

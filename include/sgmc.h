@@ -164,6 +164,14 @@ sg_status sg_measure_device(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintpt
  * synchronises. */
 sg_status sg_measure_async(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
 
+/* n_mcs MCS as sg_run_mcs, then the observables of the resulting state into HOST
+ * buffers as sg_measure_async (same buffers, staging and waiting rules).  When the
+ * sweep kernel holds both one-word chains of a sample in each CTA (n_chains == 2,
+ * n_temps <= 32, the fused exchange, a launch shape of two words per CTA) the
+ * measurement runs inside the last MCS's launch, from the lattice in shared memory;
+ * otherwise the two calls run one after the other.  SG_EINVAL if n_mcs < 1. */
+sg_status sg_run_mcs_measure_async(sg_handle *h, int32_t n_mcs, int32_t *E_out, int32_t *Q_out, uintptr_t stream);
+
 /* Wait for every copy that sg_measure_async has enqueued on the handle's copy stream.
  * sg_restore and sg_destroy wait for them too before they touch or release anything. */
 sg_status sg_measure_wait(sg_handle *h);

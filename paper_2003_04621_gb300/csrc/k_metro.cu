@@ -196,7 +196,7 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
 // n_mcs MCS.  When the job's `fuse` flag is set the item holds whole chains (a chain is
 // Wc <= WPC words) and their exchange passes run between the MCS.  The job comes from a
 // table in parameter space, so one launch can sweep many jobs of one lattice shape.
-template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ>
+template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false>
 __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     k_resident_packed(const __grid_constant__ ResidentParams<MAXJ> rp) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -381,6 +381,59 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     }
   }
 
+  if constexpr (MEAS) {
+    // fused measurement (the launcher checked: two one-word chains held, exchange fused):
+    // E by slot from the held energies and maps, and N q of the 32 pairs from one xor
+    // per site of chain 0's word with chain 1's word moved into chain-0 lane order (lane
+    // b -> perm0[slot1[b]]) by byte tables, which take the no longer needed pair tables
+    const int T = jb.T;
+    for (int e = tid; e < 2 * T; e += NT) {
+      const int ci = e >= T ? 1 : 0, k = e - ci * T;
+      rp.mE[((size_t)s * 2 + ci) * T + k] = EL(ci)[PM(ci)[k]];
+    }
+    if (rp.mQ != nullptr) {
+      uint32_t *sig = reinterpret_cast<uint32_t *>(pair_tab); // 1024 words = the 2 x 256 uint2 tables
+      uint32_t *tot = reinterpret_cast<uint32_t *>(epart);    // [32] disagreeing sites per pair
+      for (int e = tid; e < 1024; e += NT) {
+        const int j = e >> 8, v = e & 255;
+        uint32_t o = 0u;
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb) {
+          const int b = 8 * j + bb;
+          if (((v >> bb) & 1) && b < T) o |= 1u << PM(0)[SL(1)[b]];
+        }
+        sig[e] = o;
+      }
+      if (tid < 32) tot[tid] = 0u;
+      __syncthreads();
+      uint32_t Vq[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Vq[b] = 0u;
+      const int n4 = g.N >> 2; // every extent is even: N is a multiple of 4
+      const int iters = (n4 + NT - 1) / NT;
+      for (int it = 0; it < iters; ++it) {
+        const int i = it * NT + tid;
+        if (i < n4) {
+          const uint4 a4 = reinterpret_cast<const uint4 *>(sp)[i];
+          const uint4 b4 = reinterpret_cast<const uint4 *>(sp + g.N)[i];
+          const uint32_t q0 = a4.x ^ permute_word(sig, b4.x), q1 = a4.y ^ permute_word(sig, b4.y);
+          const uint32_t q2 = a4.z ^ permute_word(sig, b4.z), q3 = a4.w ^ permute_word(sig, b4.w);
+          uint32_t s1, cy1;
+          fadd(q0, q1, q2, s1, cy1);
+          const uint32_t cc = s1 & q3;
+          vcount_add(Vq, s1 ^ q3, cy1 ^ cc, cy1 & cc);
+        }
+        if ((it + 1) % 63 == 0 || it + 1 == iters) { // before 8 planes can overflow; warp-uniform
+          const int32_t v = warp_lane_sum(Vq);
+          if (v) atomicAdd(&tot[lane], (uint32_t)v);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) Vq[b] = 0u;
+        }
+      }
+      __syncthreads();
+      if (tid < T) rp.mQ[(size_t)s * T + SL(0)[tid]] = g.N - 2 * (int32_t)tot[tid];
+    }
+  }
   if (nch > 0 && warp < WPC && lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = EL(my_ci)[my_j0 + lane];
   if (warp < nch) {
     const size_t cb = ((size_t)s * jb.C + c0 + warp) * jb.T;
@@ -614,14 +667,18 @@ int8_fn pick_int8(int d) {
 template <int MAXJ>
 using packed_fn = void (*)(ResidentParams<MAXJ>);
 
-template <int D, int WPC, bool EONLY, int MAXJ>
+template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false>
 packed_fn<MAXJ> pick_packed_nt(int nt) {
   switch (nt) {
-  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ>;
-  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ>;
-  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ>;
-  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ>;
+  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS>;
+  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS>;
+  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS>;
+  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS>;
   }
+}
+// the sweep kernel that measures after its last MCS (two one-word chains per CTA)
+packed_fn<1> pick_packed_meas(int d, int nt) {
+  return d == 2 ? pick_packed_nt<2, 2, false, 1, true>(nt) : pick_packed_nt<3, 2, false, 1, true>(nt);
 }
 
 template <bool EONLY, int MAXJ>
@@ -632,7 +689,8 @@ packed_fn<MAXJ> pick_packed(int d, int nt, int wpc) {
 } // namespace
 
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
-                            bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro) {
+                            bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
+                            int32_t *meas_E, int32_t *meas_Q) {
   if (int8fmt) {
     int8_fn fn;
     if (energy_only && fuse_pt) fn = pick_int8<true, true>(jb.g.d);
@@ -646,14 +704,20 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
   rp.n_jobs = 1;
   rp.n_mcs = n_mcs;
   rp.pad0 = rp.pad1 = 0;
+  // the fused measurement needs both one-word chains of a sample in every CTA
+  const bool meas = meas_E && !energy_only && fuse_pt && jb.C == 2 && jb.Wc == 1 && wpc == 2;
+  if (meas_E && !meas) return cudaErrorInvalidValue;
+  rp.mE = meas ? meas_E : nullptr;
+  rp.mQ = meas ? meas_Q : nullptr;
   rp.jobs[0].jb = jb;
   rp.jobs[0].dv = dv;
   rp.jobs[0].first_item = 0;
   rp.jobs[0].n_items = jb.S * (jb.W / wpc);
   rp.jobs[0].fuse = fuse_pt ? 1 : 0;
   rp.jobs[0].n_metro = n_metro;
-  const packed_fn<1> fn = energy_only ? pick_packed<true, 1>(jb.g.d, nthreads, wpc)
-                                      : pick_packed<false, 1>(jb.g.d, nthreads, wpc);
+  const packed_fn<1> fn = meas          ? pick_packed_meas(jb.g.d, nthreads)
+                          : energy_only ? pick_packed<true, 1>(jb.g.d, nthreads, wpc)
+                                        : pick_packed<false, 1>(jb.g.d, nthreads, wpc);
   fn<<<(unsigned)rp.jobs[0].n_items, nthreads, smem, st>>>(rp);
   return cudaGetLastError();
 }
@@ -667,6 +731,7 @@ cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int w
     rp.n_jobs = n;
     rp.n_mcs = n_mcs;
     rp.pad0 = rp.pad1 = 0;
+    rp.mE = rp.mQ = nullptr;
     int items = 0;
     for (int i = 0; i < n; ++i) {
       rp.jobs[i] = jobs[base + i];
@@ -692,6 +757,7 @@ cudaError_t prepare_resident_kernels(int max_smem) {
         fns.push_back((const void *)pick_packed<false, 1>(d, nt, wpc));
         fns.push_back((const void *)pick_packed<true, 1>(d, nt, wpc));
         fns.push_back((const void *)pick_packed<false, MAX_BATCH_JOBS>(d, nt, wpc));
+        if (wpc == 2) fns.push_back((const void *)pick_packed_meas(d, nt));
       }
   for (int d = 2; d <= 3; ++d) {
     fns.push_back((const void *)pick_int8<false, false>(d));
@@ -738,6 +804,7 @@ cudaError_t launch_exchange_batch(JobDesc *jobs, int n_jobs, cudaStream_t st) {
     rp.n_jobs = n;
     rp.n_mcs = 1;
     rp.pad0 = rp.pad1 = 0;
+    rp.mE = rp.mQ = nullptr;
     int ctas = 0;
     for (int i = 0; i < n; ++i) {
       rp.jobs[i] = jobs[base + i];

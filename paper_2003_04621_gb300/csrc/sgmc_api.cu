@@ -338,40 +338,60 @@ cudaError_t ensure_copy_stream(sg_handle *h) {
   return e;
 }
 
-// E by slot and N q into host buffers.  `side`: copy on the handle's copy stream from
-// alternating staging slots, so that `st` goes on with its next work while the copies
-// run (not while `st` is being captured into a graph); otherwise copy on `st` from slot 0.
-sg_status measure_to_host(sg_handle *h, int32_t *E_out, int32_t *Q_out, cudaStream_t st, bool side) {
-  if (!h || !E_out) return SG_EINVAL;
-  if (h->sticky != SG_OK) return h->sticky;
-  if (h->gauss) return SG_EUNSUPPORTED;
+// Staging for a measurement into host buffers.  `side`: the copies run on the handle's
+// copy stream from alternating staging slots, so that `st` goes on with its next work
+// (not while `st` is being captured into a graph); otherwise on `st` from slot 0.  A
+// slot is rewritten only after its previous copies have finished.
+struct MeasStage {
+  bool side;
+  int slot;
+  int32_t *dE, *dQ;
+};
+
+cudaError_t measure_stage(sg_handle *h, cudaStream_t st, bool side, MeasStage *ms) {
   if (side) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) side = false;
   }
   if (side && ensure_copy_stream(h) != cudaSuccess) side = false;
   const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
-  const int slot = side ? h->mslot : 0;
+  ms->side = side;
+  ms->slot = side ? h->mslot : 0;
   if (side) h->mslot ^= 1;
-  int32_t *dE = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_E) + slot * nE;
-  int32_t *dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q) + slot * nQ;
-  const bool want_q = Q_out && h->job.C >= 2;
+  ms->dE = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_E) + ms->slot * nE;
+  ms->dQ = reinterpret_cast<int32_t *>(h->buf + h->lay.meas_Q) + ms->slot * nQ;
+  if (side && h->slot_used[ms->slot]) return cudaStreamWaitEvent(st, h->ev_done[ms->slot], 0);
+  return cudaSuccess;
+}
+
+cudaError_t measure_copy(sg_handle *h, cudaStream_t st, const MeasStage &ms, int32_t *E_out, int32_t *Q_out) {
+  const size_t nE = (size_t)h->job.S * h->job.C * h->job.T, nQ = (size_t)h->job.S * h->job.T;
   cudaError_t e = cudaSuccess;
-  // the slot is rewritten only after its previous copies have finished
-  if (side && h->slot_used[slot]) e = cudaStreamWaitEvent(st, h->ev_done[slot], 0);
-  if (e == cudaSuccess) e = launch_measure(h->job, h->dev, h->int8fmt != 0, dE, want_q ? dQ : nullptr, st);
   cudaStream_t cp = st;
-  if (side) {
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_ready[slot], st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cst, h->ev_ready[slot], 0);
+  if (ms.side) {
+    e = cudaEventRecord(h->ev_ready[ms.slot], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cst, h->ev_ready[ms.slot], 0);
     cp = h->cst;
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(E_out, dE, nE * 4, cudaMemcpyDeviceToHost, cp);
-  if (e == cudaSuccess && want_q) e = cudaMemcpyAsync(Q_out, dQ, nQ * 4, cudaMemcpyDeviceToHost, cp);
-  if (side && e == cudaSuccess) {
-    e = cudaEventRecord(h->ev_done[slot], h->cst);
-    h->slot_used[slot] = true;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(E_out, ms.dE, nE * 4, cudaMemcpyDeviceToHost, cp);
+  if (e == cudaSuccess && Q_out) e = cudaMemcpyAsync(Q_out, ms.dQ, nQ * 4, cudaMemcpyDeviceToHost, cp);
+  if (ms.side && e == cudaSuccess) {
+    e = cudaEventRecord(h->ev_done[ms.slot], h->cst);
+    h->slot_used[ms.slot] = true;
   }
+  return e;
+}
+
+// E by slot and N q into host buffers (see measure_stage for `side`).
+sg_status measure_to_host(sg_handle *h, int32_t *E_out, int32_t *Q_out, cudaStream_t st, bool side) {
+  if (!h || !E_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->gauss) return SG_EUNSUPPORTED;
+  if (h->job.C < 2) Q_out = nullptr;
+  MeasStage ms;
+  cudaError_t e = measure_stage(h, st, side, &ms);
+  if (e == cudaSuccess) e = launch_measure(h->job, h->dev, h->int8fmt != 0, ms.dE, Q_out ? ms.dQ : nullptr, st);
+  if (e == cudaSuccess) e = measure_copy(h, st, ms, E_out, Q_out);
   return check(h, e);
 }
 } // namespace
@@ -780,6 +800,32 @@ sg_status sg_measure_wait(sg_handle *h) {
   if (h->sticky != SG_OK) return h->sticky;
   if (!h->cst) return SG_OK;
   return check(h, cudaStreamSynchronize(h->cst));
+}
+
+sg_status sg_run_mcs_measure_async(sg_handle *h, int32_t n_mcs, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {
+  if (!h || n_mcs < 1 || !E_out) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  if (h->gauss) return SG_EUNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  const bool fused = !h->int8fmt && !h->global && !h->p.houdayer && h->fuse_pt && h->job.C == 2 && h->job.Wc == 1 &&
+                     h->wpc == 2;
+  if (!fused) {
+    const sg_status r = mcs_ops(h, n_mcs, st);
+    if (r != SG_OK) return r;
+    return measure_to_host(h, E_out, Q_out, st, true);
+  }
+  // the measurement runs inside the last MCS's launch, from the lattice in shared memory
+  MeasStage ms;
+  cudaError_t e = measure_stage(h, st, true, &ms);
+  if (e == cudaSuccess)
+    e = sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, true, false, h->smem, st, n_mcs, h->p.n_metro,
+                              ms.dE, Q_out ? ms.dQ : nullptr);
+  if (e == cudaSuccess) {
+    h->t_metro += (uint64_t)n_mcs * (uint64_t)h->p.n_metro;
+    h->t_pt += (uint64_t)n_mcs;
+    e = measure_copy(h, st, ms, E_out, Q_out);
+  }
+  return check(h, e);
 }
 
 sg_status sg_measure(sg_handle *h, int32_t *E_out, int32_t *Q_out, uintptr_t stream) {

@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
 
 EXPORTED = (
     "sg_query_bytes", "sg_create", "sg_sweep", "sg_exchange", "sg_houdayer", "sg_houdayer_multi", "sg_run_mcs",
-    "sg_measure", "sg_measure_device", "sg_measure_async", "sg_measure_wait", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
+    "sg_measure", "sg_measure_device", "sg_measure_async", "sg_measure_wait", "sg_run_mcs_measure_async", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
     "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_checkpoint_bytes", "sg_checkpoint",
     "sg_restore", "sg_selftest_wait", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
     "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
@@ -85,6 +85,7 @@ def lib():
         "sg_measure_device": [P, P, P, U],
         "sg_measure_async": [P, P, P, U],
         "sg_measure_wait": [P],
+        "sg_run_mcs_measure_async": [P, I32, P, P, U],
         "sg_measure_qmodes": [P, P, U],
         "sg_trips": [P, P, P, U],
         "sg_measure_qmodes_device": [P, P, U],
@@ -288,6 +289,16 @@ class Simulation:
             raise ValueError("Q must be a C-contiguous int32 array of shape [S][T]")
         _check(lib().sg_measure_async(self._h, E.ctypes.data, Q.ctypes.data if Q is not None else None,
                                       self._s(stream)), "sg_measure_async")
+
+    def run_mcs_measure_async(self, n, E, Q=None, stream=None):
+        """run_mcs(n) then measure_async(E, Q); the measurement runs inside the last MCS's
+        launch when the kernel holds both chains of a sample (see sgmc.h)."""
+        if E.dtype != np.int32 or E.shape != (self.S, self.C, self.T) or not E.flags.c_contiguous:
+            raise ValueError("E must be a C-contiguous int32 array of shape [S][C][T]")
+        if Q is not None and (Q.dtype != np.int32 or Q.shape != (self.S, self.T) or not Q.flags.c_contiguous):
+            raise ValueError("Q must be a C-contiguous int32 array of shape [S][T]")
+        _check(lib().sg_run_mcs_measure_async(self._h, int(n), E.ctypes.data, Q.ctypes.data if Q is not None else None,
+                                              self._s(stream)), "sg_run_mcs_measure_async")
 
     def measure_wait(self):
         """Wait for the copies of every measure_async call on this simulation."""

@@ -121,3 +121,35 @@ def test_plane_sums_counter_flushes(oracle_mod, dims, T):
     sim.run_mcs(2)
     orc.mcs(2)
     np.testing.assert_array_equal(sim.qmodes(), orc.qmodes())
+
+
+
+@pytest.mark.parametrize("case", ["fused", "fused_3_mcs", "houdayer", "two_words"])
+def test_run_and_measure(oracle_mod, case):
+    """sg_run_mcs_measure_async: MCS then the observables in one call, read into a pinned
+    ring.  Two one-word chains per CTA measure inside the sweep kernel's last MCS (fused,
+    also after 3 MCS in one launch); a Houdayer job and chains of two words fall back to
+    the separate kernels.  Every slot equals the oracle's measurement at that point."""
+    import torch
+
+    T = 40 if case == "two_words" else 12
+    kw = dict(ndim=3, dims=(8, 8, 8), n_samples=3, n_chains=2, temps=geometric_temps(0.5, 2.0, T), sim_seed=43,
+              houdayer=(case == "houdayer"))
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    if case.startswith("fused"):
+        sim.set_launch(256, 2)
+    per = 3 if case == "fused_3_mcs" else 1
+    n = 4
+    E = torch.empty((n, 3, 2, T), dtype=torch.int32, pin_memory=True).numpy()
+    Q = torch.empty((n, 3, T), dtype=torch.int32, pin_memory=True).numpy()
+    for k in range(n):
+        sim.run_mcs_measure_async(per, E[k], Q[k])
+    sim.measure_wait()
+    for k in range(n):
+        orc.mcs(per, houdayer=kw["houdayer"])
+        E_o, Q_o = orc.measure()
+        np.testing.assert_array_equal(E[k], E_o, err_msg=f"E slot {k}")
+        np.testing.assert_array_equal(Q[k], Q_o, err_msg=f"N q slot {k}")
+    E_s, Q_s = sim.measure()
+    np.testing.assert_array_equal(E_s, E[-1])
+    np.testing.assert_array_equal(Q_s, Q[-1])
