@@ -100,3 +100,10 @@ def test_refusals():
     with pytest.raises(SGError) as e:
         sim.set_couplings_fixed(bad)
     assert e.value.status == 1
+    # int32 host reads are the +-J jobs' (their energies are int64 here)
+    E = np.zeros((1, 2, 2), np.int32)
+    Q = np.zeros((1, 2), np.int32)
+    for call in (lambda: sim.measure_async(E, Q), lambda: sim.run_mcs_measure_async(1, E, Q)):
+        with pytest.raises(SGError) as e:
+            call()
+        assert e.value.status == 5
