@@ -485,6 +485,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   int32_t *sl = reinterpret_cast<int32_t *>(smem + L.sl);
   unsigned int *pacc = reinterpret_cast<unsigned int *>(smem + L.pacc);
   unsigned int *pnear = reinterpret_cast<unsigned int *>(smem + L.near);
+  int32_t *xch = reinterpret_cast<int32_t *>(smem + L.xch); // T <= 64: accb, rejb, uw, slow mask
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
 
   const int tid = threadIdx.x;
@@ -608,7 +609,14 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
       }
     }
     if (FUSE_PT) {
-      if (tid == 0) {
+      if (T <= 64) { // one warp: integer bounds first, the exact fp64 test only near them
+        if (tid < 32) {
+          exchange_chain_smem(T, dv.beta, pm, sl, eacc, xch, xch + 64, reinterpret_cast<uint32_t *>(xch + 128), pacc,
+                              pnear, reinterpret_cast<uint32_t *>(xch + 192), s_glob, (uint32_t)c,
+                              t_pt0 + (uint32_t)m, jb);
+          if (tid == 0) trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
+        }
+      } else if (tid == 0) {
         exchange_chain(T, dv.beta, pm, sl, eacc, s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb.sk0, jb.sk1,
                        [&](int k) { pacc[k] += 1u; }, [&]() { *pnear += 1u; });
         trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);

@@ -389,7 +389,7 @@ __host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthr
 
 // Shared-memory map of the resident int8 kernel (one chain, all its replicas).
 struct Int8Smem {
-  int spin, jbyte, jpl, thr, eacc, pm, sl, pacc, near, bar, total;
+  int spin, jbyte, jpl, thr, eacc, pm, sl, pacc, near, xch, bar, total;
 };
 __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int Tp) {
   Int8Smem L;
@@ -402,7 +402,8 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
   L.sl = L.pm + round16(4 * T);
   L.pacc = L.sl + round16(4 * T);
   L.near = L.pacc + round16(4 * T);
-  L.bar = L.near + 16;
+  L.xch = L.near + 16; // warp exchange scratch (T <= 64): bounds and words [3][64], flags [2]
+  L.bar = L.xch + (T <= 64 ? round16(4 * (3 * 64 + 2)) : 0);
   L.total = L.bar + 16;
   return L;
 }
