@@ -394,17 +394,23 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     if (rp.mQ != nullptr) {
       uint32_t *sig = reinterpret_cast<uint32_t *>(pair_tab); // 1024 words = the 2 x 256 uint2 tables
       uint32_t *tot = reinterpret_cast<uint32_t *>(epart);    // [32] disagreeing sites per pair
-      for (int e = tid; e < 1024; e += NT) {
-        const int j = e >> 8, v = e & 255;
+      uint32_t *nib = tot + 32;                                // [8][16] the permutation by nibbles
+      for (int e = tid; e < 128; e += NT) {
+        const int j = e >> 4, v = e & 15;
         uint32_t o = 0u;
 #pragma unroll
-        for (int bb = 0; bb < 8; ++bb) {
-          const int b = 8 * j + bb;
+        for (int bb = 0; bb < 4; ++bb) {
+          const int b = 4 * j + bb;
           if (((v >> bb) & 1) && b < T) o |= 1u << PM(0)[SL(1)[b]];
         }
-        sig[e] = o;
+        nib[e] = o;
       }
       if (tid < 32) tot[tid] = 0u;
+      __syncthreads();
+      for (int e = tid; e < 1024; e += NT) {
+        const int j = e >> 8, v = e & 255;
+        sig[e] = nib[(2 * j) * 16 + (v & 15)] | nib[(2 * j + 1) * 16 + (v >> 4)];
+      }
       __syncthreads();
       uint32_t Vq[NB];
 #pragma unroll
