@@ -153,3 +153,18 @@ def test_run_and_measure(oracle_mod, case):
     E_s, Q_s = sim.measure()
     np.testing.assert_array_equal(E_s, E[-1])
     np.testing.assert_array_equal(Q_s, Q[-1])
+
+
+def test_run_and_measure_one_chain(oracle_mod):
+    """With one chain there is no overlap: the call returns E by slot only."""
+    import torch
+
+    kw = dict(ndim=2, dims=(16, 16), n_samples=2, n_chains=1, temps=geometric_temps(0.5, 2.0, 20), sim_seed=47)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    E = torch.empty((3, 2, 1, 20), dtype=torch.int32, pin_memory=True).numpy()
+    for k in range(3):
+        sim.run_mcs_measure_async(2, E[k])
+    sim.measure_wait()
+    for k in range(3):
+        orc.mcs(2)
+        np.testing.assert_array_equal(E[k], orc.measure()[0], err_msg=f"E slot {k}")
