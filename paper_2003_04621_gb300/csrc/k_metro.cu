@@ -51,7 +51,7 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__re
                                            const uint8_t *__restrict__ jbyte,
                                            const uint2 *__restrict__ pair_tab, const uint32_t *vmask,
                                            const int *ngroups, const uint32_t *c3base, const PhiloxSweep &P,
-                                           const Job &jb, uint32_t (&V)[WPC][NB]) {
+                                           const Job &jb, uint32_t (&V)[WPC][NB], int wcount = WPC) {
   const int H = g.H, L1 = g.L1, Nh = g.Nh, N = g.N;
   for (int q = threadIdx.x; q < Nh; q += NT) {
     const int row = q / H;
@@ -84,6 +84,7 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__re
     if (!NOFLIP) Q = philox_site(P, (uint32_t)(g.L0 * row + 2 * k + xodd), jb);
 #pragma unroll
     for (int w = 0; w < WPC; ++w) {
+      if (NOFLIP && w >= wcount) continue; // counting only the first wcount words
       uint32_t *own = sp + w * N + col * Nh;
       const uint32_t *oth = sp + w * N + (1 - col) * Nh;
       uint32_t nb[2 * D];
@@ -234,6 +235,9 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   auto TN = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 580); };
   auto TSUM = [&](int ci) { return reinterpret_cast<unsigned long long *>(ptw + ci * PT_WORDS + 582); };
   const bool track = dv.trip_dir != nullptr;
+  // energies after a Houdayer move (pad0 = 1): the move conserves E_a + E_b of the pair at
+  // each slot, so only chain 0's words are counted and chain 1's energies follow
+  const bool conserve = ENERGY_ONLY && MAXJ == 1 && WPC == 2 && rp.pad0 == 1 && JD.fuse && jb.C == 2 && jb.Wc == 1;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -327,7 +331,8 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         half_sweep<D, NT, WPC, false, false>(g, 0, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
         __syncthreads();
       }
-      half_sweep<D, NT, WPC, true, ENERGY_ONLY>(g, 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
+      half_sweep<D, NT, WPC, true, ENERGY_ONLY>(g, 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V,
+                                                conserve ? 1 : WPC);
 #pragma unroll
       for (int w = 0; w < WPC; ++w) epart[w * NT + tid] = warp_lane_sum(V[w]);
       __syncthreads();
@@ -340,6 +345,16 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         else if (lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = 2 * U - D * g.N;
       }
       __syncthreads();
+      if (conserve) {
+        // slot k pairs chain-0 replica a = perm0[k] with chain-1 replica b = perm1[k]; the
+        // global energies are still those before the move
+        if (warp == 1 && lane < jb.T) {
+          const size_t cb0 = (size_t)s * 2 * jb.T, cb1 = cb0 + jb.T;
+          const int a = PM(0)[lane], b = PM(1)[lane];
+          EL(1)[b] = dv.E[cb0 + a] + dv.E[cb1 + b] - EL(0)[a];
+        }
+        __syncthreads();
+      }
     }
     if (nch > 0) {
       // warp ci exchanges chain ci, then refreshes the tables of the chain's words
@@ -704,7 +719,7 @@ packed_fn<MAXJ> pick_packed(int d, int nt, int wpc) {
 
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
-                            int32_t *meas_E, int32_t *meas_Q) {
+                            int32_t *meas_E, int32_t *meas_Q, bool after_move) {
   if (int8fmt) {
     int8_fn fn;
     if (energy_only && fuse_pt) fn = pick_int8<true, true>(jb.g.d);
@@ -717,7 +732,8 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
   ResidentParams<1> rp;
   rp.n_jobs = 1;
   rp.n_mcs = n_mcs;
-  rp.pad0 = rp.pad1 = 0;
+  rp.pad0 = energy_only && after_move ? 1 : 0;
+  rp.pad1 = 0;
   // the fused measurement needs both one-word chains of a sample in every CTA
   const bool meas = meas_E && !energy_only && fuse_pt && jb.C == 2 && jb.Wc == 1 && wpc == 2;
   if (meas_E && !meas) return cudaErrorInvalidValue;

@@ -565,8 +565,10 @@ sg_status mcs_ops(sg_handle *h, int n_mcs, cudaStream_t st) {
     if (r == SG_OK && h->p.houdayer) {
       r = houdayer_move(h, st, h->p.houdayer == 2);
       if (r == SG_OK && h->fuse_pt && !h->global) {
-        // energies after the move, then the exchange, in one resident launch
-        r = launch_resident<true, true>(h, st, 1, 1);
+        // energies after the move, then the exchange, in one resident launch (chain 1's
+        // energies from the conserved pair sums when a CTA holds both chains)
+        r = check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, true, true, h->smem, st, 1, 1, nullptr,
+                                           nullptr, true));
         if (r == SG_OK) h->t_pt += 1;
         if (r != SG_OK) return r;
         continue;

@@ -139,7 +139,8 @@ template <int MAXJ>
 struct ResidentParams {
   int n_jobs;
   int n_mcs;
-  int pad0, pad1;
+  int pad0; // energy-only single-job launches: 1 right after a Houdayer move (E_a + E_b kept)
+  int pad1;
   // single-job launches of two one-word chains per CTA: after the last MCS, E by slot
   // [S][2][T] and N q [S][T] into these device arrays (null: no measurement)
   int32_t *mE, *mQ;
@@ -411,7 +412,7 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 // Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
-                            int32_t *meas_E = nullptr, int32_t *meas_Q = nullptr);
+                            int32_t *meas_E = nullptr, int32_t *meas_Q = nullptr, bool after_move = false);
 // Several jobs of the same lattice shape in one launch (chunks of MAX_BATCH_JOBS).
 // jobs[i].n_items/fuse/n_metro must be filled; first_item is set here.
 cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int wpc, size_t smem, cudaStream_t st,
