@@ -445,31 +445,31 @@ def main():
     # MCS and a device->host read of that step's observables (E by slot and N q) into its
     # own slot of a pinned ring; the copies run on the simulation's copy stream while the
     # next MCS runs, and the timed region ends when the last has landed
-    e2e = None
-    if rank == 0 or ws > 1:
-        E = torch.empty((args.steps, w.n_samples, w.n_chains, w.T), dtype=torch.int32, pin_memory=True).numpy()
-        Q = torch.empty((args.steps, w.n_samples, w.T), dtype=torch.int32, pin_memory=True).numpy()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim2 = Simulation(stream=stream, **kw)
-        sim2.set_launch(launch["threads"], launch["words"])
-        for k in range(args.steps):
-            sim2.run_mcs_measure_async(1, E[k], Q[k], stream=stream)
-        sim2.measure_wait()
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        E_last, Q_last = sim2.measure(stream=stream)  # a synchronous read: the ring's last slot
-        if not (np.array_equal(E_last, E[-1]) and np.array_equal(Q_last, Q[-1])):
-            raise RuntimeError("asynchronous and synchronous measurements differ")
-        d2h = E[0].nbytes + Q[0].nbytes
-        h2d = (w.T * 8 + w.T * 16) / args.steps
-        e2e = {"value": attempts_per_step * args.steps / (e2e_s * 1e9), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "includes": "create (H2D tables, device init) + per step one MCS and a D2H read of E and q "
-                           "into a pinned per-step ring (the measurement inside the MCS launch where the kernel "
-                           "holds both chains, copies on the simulation's copy stream overlapping the next MCS); "
-                           "timed until all have landed"}
-        sim2.close()
+    # every rank runs its shard end to end; the whole job's time is the slowest rank's
+    E = torch.empty((args.steps, w.n_samples, w.n_chains, w.T), dtype=torch.int32, pin_memory=True).numpy()
+    Q = torch.empty((args.steps, w.n_samples, w.T), dtype=torch.int32, pin_memory=True).numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim2 = Simulation(stream=stream, **kw)
+    sim2.set_launch(launch["threads"], launch["words"])
+    for k in range(args.steps):
+        sim2.run_mcs_measure_async(1, E[k], Q[k], stream=stream)
+    sim2.measure_wait()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    E_last, Q_last = sim2.measure(stream=stream)  # a synchronous read: the ring's last slot
+    if not (np.array_equal(E_last, E[-1]) and np.array_equal(Q_last, Q[-1])):
+        raise RuntimeError("asynchronous and synchronous measurements differ")
+    d2h = (E[0].nbytes + Q[0].nbytes) * ws
+    h2d = (w.T * 8 + w.T * 16) * ws / args.steps
+    e2e = {"value": attempts_per_step * ws * args.steps / (e2e_s * 1e9), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "includes": "create (H2D tables, device init) + per step one MCS and a D2H read of E and q "
+                       "into a pinned per-step ring (the measurement inside the MCS launch where the kernel "
+                       "holds both chains, copies on the simulation's copy stream overlapping the next MCS); "
+                       "timed until all have landed; whole job over all ranks (slowest rank's time)"}
+    sim2.close()
 
     pk, pk_kind = peaks()
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
