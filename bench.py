@@ -95,31 +95,98 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int):
+def cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', or the Arm implementer/part)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(workload, n_threads: int, n_mcs: int, n_samples: int, metropolis_only: bool = False):
     """Time the CPU oracle, as it is, on `n_samples` samples of the workload for `n_mcs`
-    MCS each (with the workload's Houdayer moves), one oracle per thread (ctypes
-    releases the GIL)."""
+    MCS each (with the workload's Houdayer moves), or `n_mcs` Metropolis sweeps alone,
+    one oracle per thread (ctypes releases the GIL).  The oracles are created untimed."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
     oracle.build()
     per = max(1, n_samples // n_threads)
-    shards = [(t * per, per) for t in range(n_threads)]
-
-    def run(shard):
-        off, S = shard
-        o = oracle.Oracle(oracle.OracleParams(workload.ndim, workload.dims, S, workload.n_chains,
+    orcs = [oracle.Oracle(oracle.OracleParams(workload.ndim, workload.dims, per, workload.n_chains,
                                               list(workload.temps), coupling_seed=workload.coupling_seed,
-                                              sim_seed=workload.sim_seed, sample_offset=off))
-        o.mcs(n_mcs, houdayer=bool(workload.houdayer))
-        return S
+                                              sim_seed=workload.sim_seed, sample_offset=t * per))
+            for t in range(n_threads)]
+
+    def run(o):
+        if metropolis_only:
+            o.sweep(n_mcs)
+        else:
+            o.mcs(n_mcs, houdayer=bool(workload.houdayer))
+        return o.S
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=n_threads) as ex:
-        done = sum(ex.map(run, shards))
+        done = sum(ex.map(run, orcs))
     dt = time.perf_counter() - t0
     attempts = workload.N * workload.n_chains * workload.T * done * n_mcs
     return attempts / (dt * 1e9), dt, done
+
+
+def cpu_baselines(w, houd: bool) -> dict:
+    """The oracle on the host: all cores (one thread per sample) and one thread, full MCS
+    and Metropolis sweeps alone; the all-core full-MCS figure is the headline value."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    mcs = 8 if houd else 120  # a few seconds of oracle work per figure
+    v, dt, done = cpu_baseline(w, cores, mcs, cores)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+           "build": "gcc " + " ".join(oracle.CFLAGS),
+           "sample": f"{done} of the {w.n_samples} samples x {mcs} MCS, one oracle thread per sample "
+                     f"({dt:.1f} s wall, {dt * cores:.0f} core-s)"}
+    v1, dt1, _ = cpu_baseline(w, 1, max(1, mcs // 4), 1)
+    out["one_thread"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": f"1 sample x {max(1, mcs // 4)} MCS "
+                                                                            f"({dt1:.1f} s)"}
+    vm, dtm, donem = cpu_baseline(w, cores, mcs, cores, metropolis_only=True)
+    out["metropolis_only"] = {"value": vm, "unit": UNIT, "cores": cores,
+                              "sample": f"{donem} samples x {mcs} Metropolis sweeps ({dtm:.1f} s)"}
+    vm1, dtm1, _ = cpu_baseline(w, 1, max(1, mcs // 4), 1, metropolis_only=True)
+    out["metropolis_only_one_thread"] = {"value": vm1, "unit": UNIT, "cores": 1,
+                                         "sample": f"1 sample x {max(1, mcs // 4)} Metropolis sweeps ({dtm1:.1f} s)"}
+    return out
+
+
+def philox_ceiling(stream, attempts_per_step: int, reps: int = 5) -> dict:
+    """Time the Philox-only probe (sg_probe_philox: the sweep's Philox work and nothing
+    else, same launch shape) over as many words as one MCS of the workload draws; the
+    median rate is the ceiling the sweep's attempts/ns is reported against."""
+    import torch
+
+    from paper_2003_04621_gb300.sgmc import probe_philox
+
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 3 * n_sm
+    out = torch.zeros(blocks * 256, dtype=torch.int32, device="cuda")
+    n_sites = max(1, attempts_per_step // 64)
+    probe_philox(n_sites, 1, blocks, out, stream=stream)
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        words = probe_philox(n_sites, 1, blocks, out, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    med = statistics.median(ms)
+    return {"words_per_ns": words / (med * 1e6), "ms": med, "words": words, "blocks": blocks, "threads": 256}
 
 
 def run_reference(args, ws, rank):
@@ -474,7 +541,11 @@ def main():
     pk, pk_kind = peaks()
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    # ALU roofline: lane-instructions per second at the sampled SM clock (4 schedulers x 32
+    # the binding bound: the Philox words the sweep must draw, one per attempt, measured
+    # live by the Philox-only probe on the same launch shape
+    ceiling = philox_ceiling(stream, attempts_per_step)
+    kernel_rate = attempts_per_step / (mean_launch_ms * 1e6)  # attempts/ns of the timed launch
+    # issue rate: lane-instructions per second at the sampled SM clock (4 schedulers x 32
     # lanes x 1 instruction per clock per SM), against the algorithmic instructions of an
     # attempt: Philox4x32-10 costs 10 rounds x (2 wide multiplies + 2 three-input xors) per
     # 4 words = 10 per attempt, plus the compare and the accept-bit insert = 12.
@@ -508,12 +579,19 @@ def main():
         "gpu_launches": args.steps * launches_per_step,
         "wall_s": wall,
         "clocks": clk,
-        "roofline": {"bound": "alu", "achieved": achieved_tips, "peak": peak_tips, "unit": "Tinstr/s",
-                     "frac": achieved_tips / peak_tips, "traffic": traffic if not houd else None,
+        "roofline": {"bound": "alu", "achieved": kernel_rate, "peak": ceiling["words_per_ns"], "unit": "attempts/ns",
+                     "frac": kernel_rate / ceiling["words_per_ns"], "traffic": traffic if not houd else None,
                      "kernel": f"k_resident_packed<{w.ndim},{launch['threads']},{launch['words']},fused exchange>"
                      if not houd else "whole MCS (5 kernels; see profiles/)",
-                     "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled)",
-                     "instr_per_attempt": instr_per_attempt},
+                     "peak_kind": "measured live: Philox-only probe (sg_probe_philox), the sweep's Philox words "
+                                  f"of one MCS ({ceiling['words']}) on {ceiling['blocks']} CTAs x 256 threads, "
+                                  f"median of 5: {ceiling['ms']:.4f} ms",
+                     "traffic_note": "DRAM bytes of one launch (ncu, profiles/); its updated words (4 N W S bytes) "
+                                     "stay dirty in L2 and are written back during the next step's L2 flush, "
+                                     "outside the timed launch",
+                     "issue": {"achieved": achieved_tips, "peak": peak_tips, "unit": "Tinstr/s",
+                               "frac": achieved_tips / peak_tips, "instr_per_attempt": instr_per_attempt,
+                               "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled)"}},
         "hbm_effective": {"achieved_gbs": hbm_eff, "peak_gbs": pk["hbm_gbs"], "frac": hbm_eff / pk["hbm_gbs"],
                           "peak_kind": pk_kind, "bytes_per_attempt": BYTES_PER_ATTEMPT},
         "e2e": e2e,
@@ -523,12 +601,7 @@ def main():
         line["serving"] = bench_serving(args.serve_jobs)
         line["extensions"] = bench_extensions(stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
-        mcs = 8 if houd else 120  # about 20 s of oracle work on 16 cores
-        v, dt, done = cpu_baseline(w, cores, mcs, cores)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{done} of the {w.n_samples} samples x {mcs} MCS, one oracle thread per "
-                                          f"sample ({dt:.1f} s wall, {dt * cores:.0f} core-s)"}
+        line["cpu_baseline"] = cpu_baselines(w, houd)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

@@ -234,6 +234,18 @@ sg_status sg_get_state(sg_handle *h, int32_t *E_out, int32_t *perm_out, uint64_t
 sg_status sg_counters(sg_handle *h, uint64_t *near_threshold, uint64_t *pt_accepts,
                       uint64_t *houdayer_sites, uintptr_t stream);
 
+/* How often the fast screens of the fused kernels deferred to the exact rule (HOST
+ * buffers; synchronises `stream`; either pointer may be NULL).  These decisions are the
+ * plain fp64 / fixed-function ones in every case; the counts show that those paths ran.
+ *   exchange_exact   exchange decisions (Eq. 5) of the one-warp exchanges inside the
+ *                    sweep kernels whose draw u fell within the fp32 screening margin of
+ *                    the threshold (or u = 0), so that exp(delta) was evaluated in fp64
+ *   metropolis_band  general-coupling Metropolis draws (Sec. 2.1) that fell inside the
+ *                    2^-14 band around the hardware-exp estimate of the threshold, so
+ *                    that the fixed fp32 threshold floor(e 2^32) was evaluated */
+sg_status sg_exact_path_counters(sg_handle *h, uint64_t *exchange_exact, uint64_t *metropolis_band,
+                                 uintptr_t stream);
+
 /* Metropolis thresholds thr[k][m-1] = min(floor(exp(-4 m beta_k) 2^32), 2^32 - 1),
  * m = 1..ndim, computed on the host in fp64 (HOST buffer [n_temps][ndim]). */
 sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out);
@@ -276,14 +288,16 @@ void sg_batch_destroy(sg_batch *b);
  * to 4096 (sample, word) pairs: lane-pair tables and bond sums), which every GPU that
  * loads the library keeps until the process exits.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  Every call uses the same array and clears what
- * must start at zero, so calls whose work overlaps on the GPU (other streams, other
- * threads, other handles) race and must be serialised by the caller.
+ * first call before any stream capture.  The address is kept for the life of the process,
+ * so the library must not outlive a reset of the device (cudaDeviceReset, or a new
+ * primary context on it): after one, this call would use a stale address.  Every call
+ * uses the same array and clears what must start at zero, so calls whose work overlaps
+ * on the GPU (other streams, other threads, other handles) race and must be serialised
+ * by the caller.
  * Errors: SG_ELIMIT if n_samples x words per site exceeds 4096 (words per site =
  * n_chains x ceil(n_temps / 32)); SG_EUNSUPPORTED for int8 spins. */
 sg_status sg_sweep_streaming_static(sg_handle *h, int32_t n_sweeps, uintptr_t stream);
 
-/* Free the host-side handle.  The caller frees the device buffer afterwards. */
 /* Checkpoint and resume (long runs): a checkpoint is a host blob of
  * sg_checkpoint_bytes bytes holding the parameters that fix the layout and the
  * dynamics, the temperatures, the step counters and the handle's whole device buffer.
@@ -301,6 +315,19 @@ sg_status sg_restore(sg_handle *h, const void *host_in, size_t bytes, uintptr_t 
  * SG_ETIMEOUT), exactly as after a copy that never landed.  No fault, trap or hang. */
 sg_status sg_selftest_wait(sg_handle *h, int32_t max_tries, uintptr_t stream);
 
+/* Measurement probe (not a step of the paper's method): the Philox work of n_sweeps
+ * packed sweeps over n_sites sites of two 32-replica words each -- the draws of one
+ * Philox4x32-10 word per attempt (Sec. 3), with the rounds that a sweep and a site share
+ * computed once, as the sweep kernel does -- and nothing else.  Its rate, 64 n_sites
+ * n_sweeps words over the time it takes, is an upper bound on the sweep's attempts per
+ * ns.  Launches n_blocks CTAs of 256 threads on `stream` (enqueued only; the caller
+ * times it).  `out`: DEVICE buffer of n_blocks x 256 uint32 that the kernel may write
+ * (its outputs are folded into a value that is stored only if it matches a sentinel, so
+ * no work is optimised away).  SG_EINVAL for sizes below 1 or a NULL buffer. */
+sg_status sg_probe_philox(int32_t n_sites, int32_t n_sweeps, int32_t n_blocks, uint64_t sim_seed, uint32_t *out,
+                          uintptr_t stream);
+
+/* Free the host-side handle.  The caller frees the device buffer afterwards. */
 void sg_destroy(sg_handle *h);
 
 /* Static description of a status code. */

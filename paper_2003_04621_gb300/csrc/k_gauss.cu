@@ -112,7 +112,7 @@ __host__ __device__ inline GaussSmem gauss_smem(int N, int d, int T, int Tp) {
 __device__ void exchange_chain64_warp(int T, const double *beta, int32_t *perm, int32_t *slot, const long long *E,
                                       long long *accb, long long *rejb, uint32_t *uw, uint8_t *slow,
                                       uint32_t s_glob, uint32_t c, uint32_t t, uint32_t k0, uint32_t k1,
-                                      unsigned int *pacc, unsigned int *pnear) {
+                                      unsigned int *pacc, unsigned int *pnear, unsigned int *pexact) {
   const int lane = threadIdx.x & 31;
   for (int k = lane; k + 1 < T; k += 32) {
     const uint32_t u = philox10((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, k0, k1).x;
@@ -156,6 +156,7 @@ __device__ void exchange_chain64_warp(int T, const double *beta, int32_t *perm, 
         const double x = __dmul_rn((double)uw[k], 0x1p-32);
         const double e = exp(delta);
         if (fabs(__dsub_rn(x, e)) < 1e-12) *pnear += 1u;
+        *pexact += 1u;
         accept = x < e;
       }
       if (accept) {
@@ -186,6 +187,8 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
   int32_t *sl = reinterpret_cast<int32_t *>(smem + L.sl);
   unsigned int *pacc = reinterpret_cast<unsigned int *>(smem + L.pacc);
   unsigned int *pnear = reinterpret_cast<unsigned int *>(smem + L.near);
+  unsigned int *pexact = pnear + 1; // exchange decisions by the exact test
+  unsigned int *pband = pnear + 2;  // Metropolis draws inside the screening band
   long long *accb = reinterpret_cast<long long *>(smem + L.accb);
   long long *rejb = reinterpret_cast<long long *>(smem + L.rejb);
   uint32_t *uw = reinterpret_cast<uint32_t *>(smem + L.uw);
@@ -216,7 +219,11 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
     sl[j] = dv.slot[chain_base + j];
     pacc[j] = 0u;
   }
-  if (tid == 0) *pnear = 0u;
+  if (tid == 0) {
+    *pnear = 0u;
+    *pexact = 0u;
+    *pband = 0u;
+  }
   __syncthreads();
   for (int j = tid; j < Tp; j += GNT) betaf[j] = j < T ? __double2float_rn(dv.beta[sl[j]]) : 0.0f;
   const bool ok = mbar_wait(bar, 0, MBAR_MAX_TRIES);
@@ -235,6 +242,7 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
   // sites q = tid / G, tid / G + GNT / G, ...; its energy terms stay in registers and are
   // summed over the warp's lanes of the same group before one shared add each
   const bool fixed_g = (GNT % G) == 0;
+  uint32_t nband = 0u; // this thread's draws that took the exact threshold
   const int n_outer = ENERGY_ONLY ? 1 : n_mcs;
   const int n_inner = ENERGY_ONLY ? 1 : n_metro;
   for (int m = 0; m < n_outer; ++m) {
@@ -288,6 +296,7 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
               near |= (f == 0 ? 1u : 0u) << r;
             }
             if (near) {
+              nband += __popc(near & (T - 4 * gi >= 4 ? 0xFu : ((1u << (T - 4 * gi)) - 1u)));
 #pragma unroll
               for (int r = 0; r < 4; ++r)
                 if ((near >> r) & 1u)
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
     if (FUSE_PT) {
       if (tid < 32) {
         exchange_chain64_warp(T, dv.beta, pm, sl, reinterpret_cast<const long long *>(eacc), accb, rejb, uw, slowf,
-                              s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb.sk0, jb.sk1, pacc, pnear);
+                              s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb.sk0, jb.sk1, pacc, pnear, pexact);
         if (tid == 0) trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
       }
       __syncthreads();
@@ -347,7 +356,12 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
       if (j + 1 < T && pacc[j]) atomicAdd(&dv.ctr[CTR_PT + j], (unsigned long long)pacc[j]);
     }
   }
+  nband = __reduce_add_sync(0xFFFFFFFFu, nband);
+  if ((tid & 31) == 0 && nband) atomicAdd(pband, nband);
+  __syncthreads();
   if (FUSE_PT && tid == 0 && *pnear) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*pnear);
+  if (FUSE_PT && tid == 0 && *pexact) atomicAdd(&dv.ctr[CTR_XEXACT], (unsigned long long)*pexact);
+  if (tid == 0 && *pband) atomicAdd(&dv.ctr[CTR_GBAND], (unsigned long long)*pband);
   if (!ENERGY_ONLY) {
     fence_proxy_async();
     __syncthreads();

@@ -123,8 +123,8 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__re
 __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, int32_t *pm, int32_t *sl,
                                                     const int32_t *el, int32_t *accb, int32_t *rejb,
                                                     uint32_t *uw, unsigned int *pacc, unsigned int *pnear,
-                                                    uint32_t *slowmask, uint32_t s_glob, uint32_t c, uint32_t t,
-                                                    const Job &jb) {
+                                                    unsigned int *pexact, uint32_t *slowmask, uint32_t s_glob,
+                                                    uint32_t c, uint32_t t, const Job &jb) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
@@ -178,6 +178,7 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
         const double x = __dmul_rn((double)uw[k], 0x1p-32);
         const double e = exp(delta);
         if (fabs(__dsub_rn(x, e)) < 1e-12) *pnear += 1u;
+        *pexact += 1u;
         accept = x < e;
       }
       if (accept) {
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   auto UW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 384); };
   auto NEAR = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 448); };
   auto SLOW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 449); };
+  auto EXACT = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 451); };
   auto TD = [&](int ci) { return ptw + ci * PT_WORDS + 452; };
   auto T0 = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 516); };
   auto TN = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 580); };
@@ -296,6 +298,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     }
     if (lane == 0) {
       *NEAR(warp) = 0u;
+      *EXACT(warp) = 0u;
       *TN(warp) = 0u;
       *TSUM(warp) = 0ull;
     }
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       // warp ci exchanges chain ci, then refreshes the tables of the chain's words
       if (warp < nch) {
         exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), ACCB(warp), REJB(warp), UW(warp),
-                            PACC(warp), NEAR(warp), SLOW(warp), s_glob, (uint32_t)(c0 + warp),
+                            PACC(warp), NEAR(warp), EXACT(warp), SLOW(warp), s_glob, (uint32_t)(c0 + warp),
                             t_pt0 + (uint32_t)m, jb);
         if (track) {
           uint32_t n_add = 0u;
@@ -472,6 +475,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       }
     }
     if (lane == 0 && *NEAR(warp)) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*NEAR(warp));
+    if (lane == 0 && *EXACT(warp)) atomicAdd(&dv.ctr[CTR_XEXACT], (unsigned long long)*EXACT(warp));
     if (track && lane == 0) {
       const size_t chain = (size_t)s * jb.C + c0 + warp;
       dv.trip_n[chain] += *TN(warp);
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   int32_t *sl = reinterpret_cast<int32_t *>(smem + L.sl);
   unsigned int *pacc = reinterpret_cast<unsigned int *>(smem + L.pacc);
   unsigned int *pnear = reinterpret_cast<unsigned int *>(smem + L.near);
-  int32_t *xch = reinterpret_cast<int32_t *>(smem + L.xch); // T <= 64: accb, rejb, uw, slow mask
+  int32_t *xch = reinterpret_cast<int32_t *>(smem + L.xch); // T <= 64: accb, rejb, uw, slow mask, exact count
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
 
   const int tid = threadIdx.x;
@@ -533,7 +537,10 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
     sl[j] = dv.slot[chain_base + j];
     pacc[j] = 0u;
   }
-  if (tid == 0) *pnear = 0u;
+  if (tid == 0) {
+    *pnear = 0u;
+    if (T <= 64) xch[194] = 0;
+  }
   __syncthreads();
   if (!ENERGY_ONLY)
     for (int j = tid; j < Tp; j += NT)
@@ -633,8 +640,8 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
       if (T <= 64) { // one warp: integer bounds first, the exact fp64 test only near them
         if (tid < 32) {
           exchange_chain_smem(T, dv.beta, pm, sl, eacc, xch, xch + 64, reinterpret_cast<uint32_t *>(xch + 128), pacc,
-                              pnear, reinterpret_cast<uint32_t *>(xch + 192), s_glob, (uint32_t)c,
-                              t_pt0 + (uint32_t)m, jb);
+                              pnear, reinterpret_cast<unsigned int *>(xch + 194),
+                              reinterpret_cast<uint32_t *>(xch + 192), s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb);
           if (tid == 0) trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
         }
       } else if (tid == 0) {
@@ -660,6 +667,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
     }
   }
   if (FUSE_PT && tid == 0 && *pnear) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*pnear);
+  if (FUSE_PT && T <= 64 && tid == 0 && xch[194]) atomicAdd(&dv.ctr[CTR_XEXACT], (unsigned long long)xch[194]);
   if (!ENERGY_ONLY) {
     fence_proxy_async();
     __syncthreads();

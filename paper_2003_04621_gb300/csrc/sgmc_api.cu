@@ -988,6 +988,24 @@ sg_status sg_counters(sg_handle *h, uint64_t *near_threshold, uint64_t *pt_accep
   return SG_OK;
 }
 
+sg_status sg_exact_path_counters(sg_handle *h, uint64_t *exchange_exact, uint64_t *metropolis_band,
+                                 uintptr_t stream) {
+  if (!h) return SG_EINVAL;
+  if (h->sticky != SG_OK) return h->sticky;
+  cudaStream_t st = as_stream(stream);
+  unsigned long long c[CTR_PT] = {0};
+  cudaError_t e = cudaMemcpyAsync(c, h->dev.ctr, sizeof(c), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return check(h, e);
+  if (c[CTR_ERROR]) {
+    h->sticky = SG_ETIMEOUT;
+    return SG_ETIMEOUT;
+  }
+  if (exchange_exact) *exchange_exact = c[CTR_XEXACT];
+  if (metropolis_band) *metropolis_band = c[CTR_GBAND];
+  return SG_OK;
+}
+
 sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out) {
   if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h || !thr_out) return SG_EINVAL;

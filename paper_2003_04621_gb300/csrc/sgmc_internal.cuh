@@ -34,7 +34,9 @@ constexpr int CTR_TMETRO = 4; // Metropolis sweeps made (the t of the sweep coun
 constexpr int CTR_TPT = 5;    // exchange passes made
 constexpr int CTR_THOUD = 6;  // Houdayer passes made
 constexpr int CTR_DONE = 7;   // finished-CTA ticket of the running kernel
-constexpr int CTR_PT = 8;     // [T-1] accepted exchanges per pair
+constexpr int CTR_XEXACT = 8; // exchange decisions of the warp exchanges decided by the exact fp64 test
+constexpr int CTR_GBAND = 9;  // general-coupling Metropolis draws inside the screening band
+constexpr int CTR_PT = 10;    // [T-1] accepted exchanges per pair
 
 constexpr unsigned long long ERR_TMA_TIMEOUT = 1ull;
 constexpr unsigned long long ERR_HOUD_ROUNDS = 2ull; // a cluster fill hit its round limit (never expected)
@@ -369,8 +371,8 @@ __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 // Shared-memory map of the resident packed kernel: `wpc` 32-replica word lattices of one
 // sample, its expanded couplings, per-lane threshold tables, energy partial sums and the
 // per-chain exchange scratch.
-// per chain (<= 64 replicas): perm, slot, E, accepts, bounds, u; flags; round-trip
-// state (direction, start) and counters
+// per chain (<= 64 replicas): perm, slot, E, accepts, bounds, u; near-threshold count,
+// slow-flag masks and exact-path count; round-trip state (direction, start) and counters
 constexpr int PT_WORDS = 9 * 64 + 8;
 struct PackedSmem {
   int spin, jbyte, jpl, thr, epart, pt, bar, total;
@@ -403,8 +405,8 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
   L.sl = L.pm + round16(4 * T);
   L.pacc = L.sl + round16(4 * T);
   L.near = L.pacc + round16(4 * T);
-  L.xch = L.near + 16; // warp exchange scratch (T <= 64): bounds and words [3][64], flags [2]
-  L.bar = L.xch + (T <= 64 ? round16(4 * (3 * 64 + 2)) : 0);
+  L.xch = L.near + 16; // warp exchange scratch (T <= 64): bounds and words [3][64], flags [2], exact count
+  L.bar = L.xch + (T <= 64 ? round16(4 * (3 * 64 + 4)) : 0);
   L.total = L.bar + 16;
   return L;
 }

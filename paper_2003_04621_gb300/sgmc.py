@@ -55,8 +55,9 @@ EXPORTED = (
     "sg_measure", "sg_measure_device", "sg_measure_async", "sg_measure_wait", "sg_run_mcs_measure_async", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
     "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_checkpoint_bytes", "sg_checkpoint",
     "sg_restore", "sg_selftest_wait", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
-    "sg_get_state", "sg_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
-    "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_destroy", "sg_strerror",
+    "sg_get_state", "sg_counters", "sg_exact_path_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
+    "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_probe_philox", "sg_destroy",
+    "sg_strerror",
 )
 
 _lib = None
@@ -102,12 +103,14 @@ def lib():
         "sg_restore": [P, P, SZ, U],
         "sg_selftest_wait": [P, I32, U],
         "sg_counters": [P, P, P, P, U],
+        "sg_exact_path_counters": [P, P, P, U],
         "sg_thresholds": [P, P],
         "sg_set_launch": [P, I32, I32],
         "sg_get_launch": [P, P, P, P],
         "sg_batch_create": [P, I32, I32, U, ctypes.POINTER(P)],
         "sg_batch_run": [P, I32, U],
         "sg_sweep_streaming_static": [P, I32, U],
+        "sg_probe_philox": [I32, I32, I32, U, P, U],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -400,8 +403,12 @@ class Simulation:
         hs = np.zeros(1, np.uint64)
         _check(lib().sg_counters(self._h, near.ctypes.data, acc.ctypes.data, hs.ctypes.data, self._s(stream)),
                "sg_counters")
+        xe = np.zeros(1, np.uint64)
+        mb = np.zeros(1, np.uint64)
+        _check(lib().sg_exact_path_counters(self._h, xe.ctypes.data, mb.ctypes.data, self._s(stream)),
+               "sg_exact_path_counters")
         return {"near_threshold": int(near[0]), "pt_accepts": acc[: self.T - 1].copy(),
-                "houdayer_sites": int(hs[0])}
+                "houdayer_sites": int(hs[0]), "exchange_exact": int(xe[0]), "metropolis_band": int(mb[0])}
 
     def set_launch(self, threads: int = 0, words: int = 0):
         """Resident-kernel launch shape (threads per CTA, words per CTA); results are
@@ -457,3 +464,13 @@ def from_workload(w, stream=None, **overrides) -> Simulation:
               houdayer=w.houdayer, sample_offset=w.sample_offset)
     kw.update(overrides)
     return Simulation(stream=stream, **kw)
+
+
+def probe_philox(n_sites: int, n_sweeps: int, n_blocks: int, out, stream=None, sim_seed: int = 1):
+    """Enqueue the Philox-ceiling probe (see sg_probe_philox) on `stream`; `out` is an
+    int32 device tensor of at least n_blocks x 256 elements.  Returns the words it draws."""
+    if out.numel() < n_blocks * 256:
+        raise ValueError("out needs n_blocks x 256 elements")
+    _check(lib().sg_probe_philox(int(n_sites), int(n_sweeps), int(n_blocks), int(sim_seed), out.data_ptr(),
+                                 _stream_handle(stream)), "sg_probe_philox")
+    return 64 * int(n_sites) * int(n_sweeps)

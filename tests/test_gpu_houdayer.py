@@ -120,11 +120,15 @@ def test_houdayer_full_size_sampled(oracle_mod):
         sim.run_mcs(1)
         E, perm, _ = sim.state()
         Em, Q = sim.measure()
+        sp = sim.spins()
         for s, o in zip(picks, orcs):
             o.mcs(1, houdayer=True)
             np.testing.assert_array_equal(E[s:s + 1], o.energies())
             np.testing.assert_array_equal(perm[s:s + 1], o.perm()[0])
+            np.testing.assert_array_equal(Em[s:s + 1], o.measure()[0])
             np.testing.assert_array_equal(Q[s:s + 1], o.measure()[1])
+            np.testing.assert_array_equal(sp[s:s + 1].cpu().numpy(), o.spins(), err_msg=f"spins {s} mcs {t}")
+        del sp
     assert sim.counters()["near_threshold"] == 0
 
 
