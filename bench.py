@@ -388,10 +388,16 @@ def bench_extensions(stream, steps: int = 5, only=None):
     return out
 
 
-def bench_serving(n_jobs: int, rate: float = 50.0, below=(2.0, 10)):
-    """Poisson(50/s, seed 7) stream of jobs served by continuous batching; p50/p99 latency.
-    `below` = (rate, jobs) repeats it at a rate under the GPU's capacity, where latency is
-    the jobs' own run time rather than time in the queue."""
+SERVING_RATES = ((50.0, 200), (10.0, 30), (5.0, 30), (2.0, 20), (1.0, 15))
+
+
+def bench_serving(rates=SERVING_RATES, quantum: int = 50):
+    """The Poisson(seed 7) stream of jobs served by continuous batching, at each (rate per
+    second, arrivals) of `rates`: the first of them is the serving workload (the first 200
+    arrivals at 50/s, above the GPU's capacity, where latency is mostly time in the queue),
+    the others a sweep of slower rates down to below saturation, where latency is the
+    jobs' own run time.  p50/p99 latency from arrival to results on the host, jobs/s and
+    served attempts/ns over the makespan."""
     import torch
 
     from paper_2003_04621_gb300.serve import Server, poisson_trace, summarize
@@ -400,7 +406,7 @@ def bench_serving(n_jobs: int, rate: float = 50.0, below=(2.0, 10)):
     arena = int(min(32 << 30, free // 3))
 
     def serve(n, r):
-        server = Server(arena_bytes=arena, quantum=100)
+        server = Server(arena_bytes=arena, quantum=quantum)
         res = summarize(server.run(poisson_trace(n, rate=r, seed=7)))
         res.update({"rate_per_s": r, "graph_builds": server.graph_builds, "graph_launches": server.graph_launches,
                     "trace": f"first {n} arrivals of the Poisson({r}/s, seed 7) stream"})
@@ -408,10 +414,9 @@ def bench_serving(n_jobs: int, rate: float = 50.0, below=(2.0, 10)):
         torch.cuda.synchronize()
         return res
 
-    out = serve(n_jobs, rate)
-    out.update({"arena_gb": arena / 2**30, "quantum_mcs": 100})
-    if below:
-        out["below_saturation"] = serve(int(below[1]), float(below[0]))
+    (r0, n0), rest = rates[0], rates[1:]
+    out = serve(n0, r0)
+    out.update({"arena_gb": arena / 2**30, "quantum_mcs": quantum, "rate_sweep": [serve(n, r) for r, n in rest]})
     return out
 
 
@@ -426,7 +431,6 @@ def main():
     ap.add_argument("--shape", default=None, help="fixed resident launch shape THREADSxWORDS (no autotuning)")
     ap.add_argument("--workload", default="3d_l16", choices=["3d_l16", "2d_l128_houdayer"],
                     help="3d_l16: the headline job; 2d_l128_houdayer: Metropolis + Houdayer + exchange")
-    ap.add_argument("--serve-jobs", type=int, default=20)
     ap.add_argument("--extension", action="append", choices=EXTENSIONS,
                     help="time only these extension rows (repeatable) and print them as one JSON line")
     args = ap.parse_args()
@@ -598,7 +602,8 @@ def main():
     }
     if ws == 1 and not args.no_extras:
         line["batched"] = bench_batched(stream, steps=max(4, args.steps // 8))
-        line["serving"] = bench_serving(args.serve_jobs)
+        line["serving"] = bench_serving()
+        line["serving"]["vs_uniform_l16"] = line["serving"]["attempts_per_ns"] / line["batched"]["uniform_l16_value"]
         line["extensions"] = bench_extensions(stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baselines(w, houd)

@@ -2,12 +2,18 @@
 
 Jobs (lattice, samples, temperatures, sweeps) arrive over time.  The server keeps a
 device-memory arena; a waiting job is admitted (first come, first served) as soon as the
-arena can hold its state, and then stays resident until it has made all its MCS.  Every
-scheduling quantum advances all resident jobs by `quantum` MCS with ONE CUDA-graph
-launch in which each job is a branch of its own (sg_batch), so jobs of different sizes
-overlap on the device; the graph is re-captured only when the set of resident jobs
-changes.  A finished job is measured (E by slot and N q, read back to the host), its
-memory is returned, and the next waiting job is admitted.
+arena can hold its state and the resident jobs do not already fill the GPU, and then
+stays resident until it has made all its MCS.  Every replay advances all resident jobs
+by the same number q of MCS with ONE CUDA-graph launch in which each job is a branch of
+its own (sg_batch), so jobs of different sizes overlap on the device; q is the scheduling
+quantum, cut to the smallest number of MCS any resident job has left, so that every job
+makes exactly its own number of MCS.  The graph is re-captured only when the resident
+set or q changes.
+
+The host never waits for a whole replay: it keeps up to two replays queued on the GPU,
+and between them it polls their completion events, admits arrivals, and retires the
+jobs whose last replay has finished (their E by slot and N q are read back on a side
+stream, their memory returned to the arena).
 
 A job's results are those of running it alone: the dynamics depend only on the job's
 own parameters, never on which other jobs share the device.
@@ -17,7 +23,6 @@ Latency is measured from a job's arrival to the moment its results are on the ho
 from __future__ import annotations
 
 import bisect
-import math
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -45,12 +50,12 @@ class JobSpec:
         return int(np.prod(self.dims)) * self.n_samples * 2 * len(self.temps) * self.n_mcs
 
 
-def poisson_trace(n_jobs: int, rate: float = 50.0, seed: int = 7, quantum: int = 100,
-                  max_sweeps: int = 5000, min_sweeps: int = 500) -> List[JobSpec]:
+def poisson_trace(n_jobs: int, rate: float = 50.0, seed: int = 7, max_sweeps: int = 5000,
+                  min_sweeps: int = 500) -> List[JobSpec]:
     """The serving workload: Poisson arrivals at `rate` per second; each job is 3D (L even
     in 8..32, temperatures geometric in [0.9, 2.0]) or 2D (L even in 32..256, [0.2, 1.6])
-    with probability 1/2, 16..256 samples, 16..40 temperatures, and a number of sweeps in
-    [min_sweeps, max_sweeps] rounded to a multiple of the scheduling quantum."""
+    with probability 1/2, 16..256 samples, 16..40 temperatures, and a number of sweeps
+    uniform in [min_sweeps, max_sweeps]."""
     rng = np.random.Generator(np.random.MT19937(seed))
     t = 0.0
     jobs = []
@@ -65,7 +70,6 @@ def poisson_trace(n_jobs: int, rate: float = 50.0, seed: int = 7, quantum: int =
         S = int(rng.integers(16, 257))
         T = int(rng.integers(16, 41))
         sweeps = int(rng.integers(min_sweeps, max_sweeps + 1))
-        sweeps = max(quantum, int(round(sweeps / quantum)) * quantum)
         jobs.append(JobSpec(j, ndim, dims, S, geometric_temps(tmin, tmax, T), sweeps, arrival=t,
                             coupling_seed=int(rng.integers(1, 2**31)), sim_seed=int(rng.integers(1, 2**31))))
     return jobs
@@ -127,47 +131,127 @@ class JobResult:
         return self.finished - self.arrival
 
 
-class Server:
-    """Continuous-batching server over one GPU (see the module docstring)."""
+class _CudaBackend:
+    """What the server needs from the device: streams, events, the SM count, and the
+    engine's binding (simulations, batches, sizes).  Tests substitute a host fake."""
 
-    def __init__(self, arena_bytes: int, quantum: int = 100, stream=None, tune: bool = False):
+    def __init__(self):
         import torch
 
-        self.arena = Arena(arena_bytes)
+        from . import sgmc
+
+        self.torch = torch
+        self.sgmc = sgmc
+
+    def stream(self):
+        return self.torch.cuda.Stream()
+
+    def event(self, stream):
+        ev = self.torch.cuda.Event()
+        ev.record(stream)
+        return ev
+
+    def n_sm(self) -> int:
+        return self.torch.cuda.get_device_properties(self.torch.cuda.current_device()).multi_processor_count
+
+    def arena(self, nbytes: int) -> "Arena":
+        return Arena(nbytes)
+
+    def query_bytes(self, spec: JobSpec) -> int:
+        p, _t = self.sgmc.make_params(spec.ndim, spec.dims, spec.n_samples, 2, list(spec.temps))
+        return self.sgmc.query_bytes(p)
+
+    def simulation(self, spec: JobSpec, ptr: int, nbytes: int, stream):
+        return self.sgmc.Simulation(spec.ndim, spec.dims, spec.n_samples, 2, list(spec.temps),
+                                    coupling_seed=spec.coupling_seed, sim_seed=spec.sim_seed, stream=stream,
+                                    device_buffer=(ptr, nbytes))
+
+    def batch(self, sims, mcs_per_launch: int, stream):
+        return self.sgmc.Batch(sims, mcs_per_launch=mcs_per_launch, stream=stream)
+
+    def synchronize(self):
+        self.torch.cuda.synchronize()
+
+
+class Server:
+    """Continuous-batching server over one GPU (see the module docstring).
+
+    quantum      MCS per replay (cut to the smallest number any resident job has left)
+    max_ctas     admission stops while the resident jobs' sweep CTAs reach this many (a
+                 few waves of the GPU: more resident jobs would only share it more
+                 thinly and delay every one of them); 0 derives it from the device
+    max_inflight replays queued on the GPU ahead of the host (2: one runs while the
+                 next waits, so the GPU never idles on the host)
+    """
+
+    def __init__(self, arena_bytes: int, quantum: int = 100, stream=None, tune: bool = False, max_ctas: int = 0,
+                 max_inflight: int = 2, backend=None):
+        self.dev = backend if backend is not None else _CudaBackend()
+        self.arena = self.dev.arena(arena_bytes)
         self.quantum = int(quantum)
-        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream = stream if stream is not None else self.dev.stream()
+        self.side = self.dev.stream()  # job creation and final measurements
         self.tune = tune
+        if max_ctas <= 0:
+            max_ctas = 12 * self.dev.n_sm()
+        self.max_ctas = int(max_ctas)
+        self.max_inflight = max(1, int(max_inflight))
         self.graph_builds = 0
         self.graph_launches = 0
 
     def _make(self, spec: JobSpec, off: int):
-        from .sgmc import Simulation
+        return self.dev.simulation(spec, self.arena.base + off, self.arena.capacity - off, self.side)
 
-        return Simulation(spec.ndim, spec.dims, spec.n_samples, 2, list(spec.temps),
-                          coupling_seed=spec.coupling_seed, sim_seed=spec.sim_seed, stream=self.stream,
-                          device_buffer=(self.arena.base + off, self.arena.capacity - off))
+    @staticmethod
+    def _ctas(sim) -> int:
+        """Sweep CTAs of one MCS of the job: (sample, word group) items of the resident
+        kernel, or for a lattice streamed from global memory its sites x words / 512
+        (one thread per site of a colour and word, 256-thread CTAs)."""
+        shape = sim.launch()
+        words = sim.C * ((sim.T + 31) // 32)
+        if shape["words"] < 0:
+            return max(1, sim.S * words * sim.N // 512)
+        return sim.S * max(1, words // max(1, shape["words"]))
 
     def run(self, trace: Sequence[JobSpec], time_scale: float = 1.0) -> List[JobResult]:
         """Serve `trace` (arrival times scaled by `time_scale`); returns one result per job."""
-        import torch
-
-        from .sgmc import Batch, make_params, query_bytes
-
         pending = deque(sorted(trace, key=lambda j: j.arrival))
         waiting: deque = deque()
         active: Dict[int, dict] = {}
         results: List[JobResult] = []
-        batch = None
-        dirty = True
+        inflight: deque = deque()  # (event, batch, job ids whose last MCS are in that replay)
+        batch, batch_key = None, None
         t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        def in_use(b):
+            return any(x is b for _, x, _ in inflight)
+
         while pending or waiting or active:
-            now = time.perf_counter() - t0
-            while pending and pending[0].arrival * time_scale <= now:
+            progressed = False
+            t = now()
+            while pending and pending[0].arrival * time_scale <= t:
                 waiting.append(pending.popleft())
-            while waiting:
+            # retire the replays that have finished, oldest first
+            while inflight and inflight[0][0].query():
+                _ev, b, fin = inflight.popleft()
+                for jid in fin:
+                    j = active.pop(jid)
+                    E, Q = j["sim"].measure(stream=self.side)
+                    results.append(JobResult(jid, j["spec"].arrival * time_scale, j["admitted"], now(),
+                                             j["spec"].attempts, E, Q))
+                    j["sim"].close()
+                    self.arena.free(j["off"], j["bytes"])
+                if b is not None and b is not batch and not in_use(b):
+                    b.close()
+                progressed = True
+            # admit waiting jobs while memory and the GPU's width allow
+            load = sum(j["ctas"] for j in active.values() if j["left"] > 0)
+            while waiting and (load < self.max_ctas or not active):
                 spec = waiting[0]
-                p, _t = make_params(spec.ndim, spec.dims, spec.n_samples, 2, list(spec.temps))
-                need = query_bytes(p)
+                need = self.dev.query_bytes(spec)
                 if need > self.arena.capacity:
                     raise ValueError(f"job {spec.job_id} needs {need} bytes, more than the arena")
                 off = self.arena.alloc(need)
@@ -175,39 +259,45 @@ class Server:
                     break
                 waiting.popleft()
                 sim = self._make(spec, off)
-                active[spec.job_id] = dict(spec=spec, sim=sim, off=off, bytes=need, left=spec.n_mcs,
-                                           admitted=time.perf_counter() - t0)
-                dirty = True
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, pending[0].arrival * time_scale - (time.perf_counter() - t0)))
-                continue
-            if dirty:
-                if batch is not None:
-                    batch.close()
-                jobs = list(active.values())
-                batch = Batch([j["sim"] for j in jobs], mcs_per_launch=self.quantum, stream=self.stream)
-                self.graph_builds += 1
-                dirty = False
-            batch.run(1, stream=self.stream)
-            self.graph_launches += 1
-            self.stream.synchronize()
-            done = []
-            for jid, j in active.items():
-                j["left"] -= self.quantum
-                if j["left"] <= 0:
-                    done.append(jid)
-            for jid in done:
-                j = active.pop(jid)
-                E, Q = j["sim"].measure(stream=self.stream)
-                fin = time.perf_counter() - t0
-                results.append(JobResult(jid, j["spec"].arrival * time_scale, j["admitted"], fin,
-                                         j["spec"].attempts, E, Q))
-                j["sim"].close()
-                self.arena.free(j["off"], j["bytes"])
-                dirty = True
+                ctas = self._ctas(sim)
+                active[spec.job_id] = dict(spec=spec, sim=sim, off=off, bytes=need, left=max(0, spec.n_mcs),
+                                           admitted=now(), ctas=ctas)
+                if spec.n_mcs <= 0:  # nothing to run: its results are those of the fresh state
+                    inflight.append((self.dev.event(self.side), None, [spec.job_id]))
+                else:
+                    load += ctas
+                progressed = True
+            # keep up to max_inflight replays queued
+            while len(inflight) < self.max_inflight:
+                run = [j for j in active.values() if j["left"] > 0]
+                if not run:
+                    break
+                q = min(self.quantum, min(j["left"] for j in run))
+                key = (tuple(j["spec"].job_id for j in run), q)
+                if key != batch_key:
+                    if batch is not None and not in_use(batch):
+                        batch.close()
+                    batch = self.dev.batch([j["sim"] for j in run], q, self.stream)
+                    batch_key = key
+                    self.graph_builds += 1
+                batch.run(1, stream=self.stream)
+                ev = self.dev.event(self.stream)
+                self.graph_launches += 1
+                fin = []
+                for j in run:
+                    j["left"] -= q
+                    if j["left"] == 0:
+                        fin.append(j["spec"].job_id)
+                inflight.append((ev, batch, fin))
+                progressed = True
+            if not progressed:
+                if inflight:
+                    time.sleep(2e-4)
+                elif pending and not waiting:
+                    time.sleep(max(0.0, pending[0].arrival * time_scale - now()))
         if batch is not None:
             batch.close()
+        self.dev.synchronize()
         return results
 
 

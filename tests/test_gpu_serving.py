@@ -2,8 +2,9 @@
 
 Small jobs arrive over a few hundredths of a second into an arena that holds only some
 of them, so jobs wait, are admitted as others finish, and share graph launches with
-different partners; each job's final E by slot and N q must equal those of the same job
-simulated on its own.
+different partners; their sweep counts are not all multiples of the scheduling quantum.
+Each job's final E by slot and N q must equal those of the same job simulated on its
+own for exactly its number of MCS.
 """
 import numpy as np
 import pytest
@@ -16,10 +17,12 @@ pytestmark = pytest.mark.gpu
 def small_trace():
     from paper_2003_04621_gb300.serve import JobSpec
 
+    # sweep counts that are and are not multiples of the quantum (100), one job with none,
+    # and one lattice streamed from global memory (240 KB per word lattice)
     specs = [
-        (3, (8, 8, 8), 40, 20, 300), (2, (48, 48), 30, 16, 200), (3, (12, 12, 12), 20, 36, 100),
-        (2, (64, 32), 24, 24, 300), (3, (6, 6, 6), 64, 12, 400), (2, (32, 32), 50, 40, 100),
-        (3, (10, 10, 10), 16, 28, 200),
+        (3, (8, 8, 8), 40, 20, 250), (2, (48, 48), 30, 16, 200), (3, (12, 12, 12), 20, 36, 137),
+        (2, (64, 32), 24, 24, 300), (3, (6, 6, 6), 64, 12, 401), (2, (32, 32), 50, 40, 37),
+        (3, (10, 10, 10), 16, 28, 200), (2, (16, 16), 8, 8, 0), (2, (256, 240), 2, 8, 30),
     ]
     jobs = []
     for k, (d, dims, S, T, mcs) in enumerate(specs):
@@ -51,6 +54,7 @@ def test_served_results_equal_jobs_run_alone():
         alone = Simulation(j.ndim, j.dims, j.n_samples, 2, list(j.temps), coupling_seed=j.coupling_seed,
                            sim_seed=j.sim_seed)
         alone.run_mcs(j.n_mcs)
+        assert alone.state()[2][1] == j.n_mcs
         E, Q = alone.measure()
         np.testing.assert_array_equal(E, r.E)
         np.testing.assert_array_equal(Q, r.Q)

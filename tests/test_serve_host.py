@@ -1,8 +1,10 @@
 """Host logic of the continuous-batching server (no GPU): the first-fit arena allocator
-over one buffer, the Poisson job trace, and the latency summary."""
+over one buffer, the Poisson job trace, the latency summary, and the scheduler run
+against a host fake of the device."""
 import numpy as np
 
-from paper_2003_04621_gb300.serve import Arena, JobResult, poisson_trace, summarize
+from paper_2003_04621_gb300.inputs import geometric_temps
+from paper_2003_04621_gb300.serve import Arena, JobResult, JobSpec, Server, poisson_trace, summarize
 
 
 def test_arena_first_fit_alignment_and_coalescing():
@@ -54,7 +56,8 @@ def test_poisson_trace_is_seeded_and_shaped():
     for j in t1:
         assert len(j.dims) in (2, 3) and all(L % 2 == 0 for L in j.dims)
         assert 16 <= j.n_samples <= 256 and 16 <= len(j.temps) <= 40
-        assert j.n_mcs % 100 == 0 and 500 <= j.n_mcs <= 5000
+        assert 500 <= j.n_mcs <= 5000
+    assert any(j.n_mcs % 100 for j in t1)  # sweep counts are not rounded to a quantum
 
 
 def test_summary_percentiles():
@@ -64,3 +67,100 @@ def test_summary_percentiles():
     lat = np.array([1.0 + i for i in range(5)])
     assert s["jobs"] == 5 and s["p50_s"] == np.percentile(lat, 50) and s["p99_s"] == np.percentile(lat, 99)
     assert abs(s["makespan_s"] - (4 + 5.0)) < 1e-12 and abs(s["attempts_per_ns"] - 5 * 10**9 / (9.0 * 1e9)) < 1e-12
+
+
+class FakeSim:
+    """A job as the scheduler sees it: its MCS so far, a launch shape, a measurement."""
+
+    def __init__(self, spec, log):
+        self.spec, self.log = spec, log
+        self.S, self.C, self.T, self.N = spec.n_samples, 2, len(spec.temps), int(np.prod(spec.dims))
+        self.mcs = 0
+        self.closed = False
+
+    def launch(self):
+        return {"threads": 256, "words": 2, "smem": 0}
+
+    def measure(self, stream=None):
+        return np.array([self.mcs]), np.array([self.spec.job_id])
+
+    def close(self):
+        self.closed = True
+
+
+class FakeEvent:
+    """Completes after a fixed number of polls (the device finishing in its own time)."""
+
+    def __init__(self, log, polls=3):
+        self.left, self.log = polls, log
+
+    def query(self):
+        self.left -= 1
+        return self.left <= 0
+
+
+class FakeBatch:
+    def __init__(self, sims, q, log):
+        self.sims, self.q, self.log, self.closed = list(sims), q, log, False
+        log["builds"].append((tuple(s.spec.job_id for s in sims), q))
+
+    def run(self, n, stream=None):
+        assert not self.closed and n == 1
+        for s in self.sims:
+            assert not s.closed
+            s.mcs += self.q
+        self.log["resident"].append(sum(s.S for s in self.sims))
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBackend:
+    def __init__(self):
+        self.log = {"builds": [], "resident": [], "events": []}
+
+    def stream(self):
+        return object()
+
+    def event(self, stream):
+        ev = FakeEvent(self.log)
+        self.log["events"].append(ev)
+        return ev
+
+    def n_sm(self):
+        return 4
+
+    def arena(self, nbytes):
+        return Arena(nbytes, device="cpu")
+
+    def query_bytes(self, spec):
+        return spec.n_samples * 1000
+
+    def simulation(self, spec, ptr, nbytes, stream):
+        return FakeSim(spec, self.log)
+
+    def batch(self, sims, q, stream):
+        return FakeBatch(sims, q, self.log)
+
+    def synchronize(self):
+        pass
+
+
+def test_scheduler_gives_every_job_exactly_its_mcs():
+    rng = np.random.default_rng(11)
+    trace = [JobSpec(k, 3, (8, 8, 8), int(rng.integers(16, 64)), geometric_temps(0.9, 2.0, 20),
+                     int(rng.integers(0, 400)), arrival=0.0005 * k) for k in range(40)]
+    dev = FakeBackend()
+    server = Server(arena_bytes=200 * 1000, quantum=100, max_ctas=150, backend=dev)
+    results = server.run(trace)
+    assert sorted(r.job_id for r in results) == list(range(40))
+    for r in results:
+        assert int(r.E[0]) == trace[r.job_id].n_mcs  # exactly n_mcs, whatever the quantum
+        assert r.finished >= r.admitted >= r.arrival - 1e-9
+    # every replay ran at most one quantum; a short replay only where some job had fewer left
+    assert all(q <= 100 for _, q in dev.log["builds"])
+    assert any(q < 100 for _, q in dev.log["builds"])
+    # the arena held the resident jobs, and admission stopped at the GPU's width (150
+    # sweep CTAs, i.e. 150 samples of two one-word chains) unless a single job exceeds it
+    assert max(dev.log["resident"]) <= 150 + 64
+    assert server.arena.free_bytes == server.arena.capacity
