@@ -314,7 +314,7 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
                       "groups in parallel"}
 
 
-EXTENSIONS = ("houdayer", "gauss", "trips", "houdayer3d")
+EXTENSIONS = ("houdayer", "gauss", "trips", "houdayer3d", "smalljob")
 
 
 def bench_extensions(stream, steps: int = 5, only=None):
@@ -377,14 +377,29 @@ def bench_extensions(stream, steps: int = 5, only=None):
             qms = timed(lambda n: [sim.qmodes_device(P, stream=stream) for _ in range(n)], steps)
             out["qmodes_l16"] = {"ms_per_measurement": qms, "pairs": u.n_samples * u.T}
         sim.close()
+    # the small int8 job (3D L=6, 8 samples x 2 chains x 12 temperatures): its 200 MCS in
+    # one launch, as the whole run would be made
+    if "smalljob" in want:
+        from paper_2003_04621_gb300.inputs import workload_3d_l6
+
+        w6 = workload_3d_l6()
+        sim = Simulation(3, w6.dims, w6.n_samples, 2, list(w6.temps), spin_format="int8", stream=stream)
+        ms = timed(lambda n: [sim.run_mcs(200, stream=stream) for _ in range(n)], steps)
+        out["int8_3d_l6_200mcs"] = {"ms_per_200_mcs": ms, "us_per_mcs": ms * 5.0,
+                                    "attempts_per_ns": w6.attempts_per_sweep * 200 / (ms * 1e6),
+                                    "workload": w6.name + " (int8, 200 MCS per launch)"}
+        sim.close()
     # the 3D L=16 job with the cluster move kept to its 8 lowest temperatures (0.9-1.1)
     if "houdayer3d" in want:
-        sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), houdayer=True, houdayer_slots=8, stream=stream)
-        sim.set_launch(256, 2)
-        ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
-        out["houdayer_3d_l16_low8"] = {"ms_per_mcs": ms, "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6),
-                                       "workload": u.name + "_houdayer_slots8"}
-        sim.close()
+        for K in (8, 32):
+            sim = Simulation(3, u.dims, u.n_samples, 2, list(u.temps), houdayer=True,
+                             houdayer_slots=K if K < u.T else 0, stream=stream)
+            sim.set_launch(256, 2)
+            ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+            out[f"houdayer_3d_l16_low{K}" if K < u.T else "houdayer_3d_l16_all"] = {
+                "ms_per_mcs": ms, "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6),
+                "workload": u.name + (f"_houdayer_slots{K}" if K < u.T else "_houdayer_all_slots")}
+            sim.close()
     return out
 
 

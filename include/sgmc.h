@@ -251,7 +251,7 @@ sg_status sg_exact_path_counters(sg_handle *h, uint64_t *exchange_exact, uint64_
 sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out);
 
 /* Launch shape of the resident sweep kernel (not part of the paper: a tuning knob).
- *   threads  CTA size: 128, 256, 512 or 1024 (0 keeps the current choice)
+ *   threads  CTA size: 64, 128, 256, 512 or 1024 (0 keeps the current choice)
  *   words    32-replica words of one sample held by one CTA: 1 or 2 (0 keeps);
  *            -1 streams the lattice from global memory instead of keeping it in a CTA
  *            (the path taken automatically when a word lattice does not fit)

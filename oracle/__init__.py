@@ -93,6 +93,7 @@ def _load():
         lib.or_get_class_stats.argtypes = [P, P, P]
         lib.or_set_counters.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
         lib.or_set_houdayer_slots.argtypes = [P, ctypes.c_int]
+        lib.or_set_typewriter.argtypes = [P, ctypes.c_int]
         lib.or_run_binned.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, P]
         lib.or_enumerate.restype = ctypes.c_int
@@ -157,6 +158,7 @@ class OracleParams:
     sim_seed: int = 1
     sample_offset: int = 0
     houdayer_slots: int = 0  # the cluster move acts on slots k < houdayer_slots (0: every slot)
+    typewriter: bool = False  # sweeps in index order (lattices with an odd extent)
 
 
 class Oracle:
@@ -190,6 +192,8 @@ class Oracle:
             if not 0 <= int(p.houdayer_slots) <= self.T:
                 raise ValueError("houdayer_slots must lie in 0..n_temps")
             lib.or_set_houdayer_slots(self._h, int(p.houdayer_slots))
+        if p.typewriter:
+            lib.or_set_typewriter(self._h, 1)
 
     def __del__(self):
         h = getattr(self, "_h", None)

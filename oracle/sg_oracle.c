@@ -147,6 +147,8 @@ typedef struct {
   uint64_t *cls_acc;   /* [T][d+1] */
   uint64_t houd_moves, houd_flipped; /* moves with M > 0, total cluster sites    */
   int houd_slots;      /* the cluster move acts on slots k < houd_slots (0: all)    */
+  int typewriter;      /* 1: sweeps visit sites in index order i = 0..N-1 (lattices  */
+                       /* with an odd extent, which have no checkerboard colouring)  */
   /* Round trips in temperature (the tunnelling time of Sec. 2.3), per replica j:   */
   int8_t *trip_dir;    /* [S][C][T] 0: no extreme seen, 1: bottom last, 2: top last */
   uint32_t *trip_t0;   /* [S][C][T] exchange pass of the trip's arrival at the bottom */
@@ -327,14 +329,18 @@ void or_destroy(or_state *st) {
 }
 
 /* ------------------------------------------------------------------------------ */
-/* Metropolis sweep (Sec. 2.4 step 1) in checkerboard order.                      */
+/* Metropolis sweep (Sec. 2.4 step 1) in checkerboard order, or in the sequential   */
+/* typewriter order i = 0..N-1 (the paper's own per-thread walk through the lattice, */
+/* Sec. 3) for lattices with an odd extent, where the two colours would not be       */
+/* independent.  The random word of an attempt is the same in both orders.           */
 /* ------------------------------------------------------------------------------ */
 static void metropolis_sweep(or_state *st) {
   const int d = st->ndim;
   const uint32_t t = st->t_metro;
-  for (int col = 0; col < 2; ++col)
+  const int passes = st->typewriter ? 1 : 2;
+  for (int col = 0; col < passes; ++col)
     for (int i = 0; i < st->N; ++i) {
-      if (colour(st, i) != col) continue;
+      if (!st->typewriter && colour(st, i) != col) continue;
       for (int s = 0; s < st->S; ++s) {
         uint32_t sg = (uint32_t)(st->s0 + s);
         for (int c = 0; c < st->C; ++c)
@@ -362,6 +368,8 @@ static void metropolis_sweep(or_state *st) {
     }
   st->t_metro++;
 }
+
+void or_set_typewriter(or_state *st, int on) { st->typewriter = on ? 1 : 0; }
 
 void or_sweep(or_state *st, int n) {
   for (int a = 0; a < n; ++a) metropolis_sweep(st);

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 from typing import Dict, Tuple
 
-SHAPES = [(nt, w) for w in (2, 1) for nt in (128, 256, 512, 1024)]
+SHAPES = [(nt, w) for w in (2, 1) for nt in (64, 128, 256, 512, 1024)]
 _cache: Dict[Tuple, Tuple[int, int]] = {}
 
 

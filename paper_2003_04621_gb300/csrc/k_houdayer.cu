@@ -22,99 +22,14 @@
 // flipping both is the exchange of the two configurations.
 // Energies are recomputed afterwards by the resident kernel (exact, bit-sliced), which
 // also runs the exchange pass when the MCS continues with it.
+#include "sgmc_houd.cuh"
 #include "sgmc_internal.cuh"
 
 namespace sgmc {
 
 namespace {
 
-constexpr uint32_t FULLM = 0xFFFFFFFFu;
 constexpr int HNT = 1024; // threads per CTA (32 warps)
-
-// Runs of an L0-bit row (RW words, bits >= L0 zero).
-// fill_up: for every run of Q holding a bit of X (X subset of Q), the bits from its lowest
-// X bit to the run's top (the carry of Q + X runs through the run and stops above it).
-template <int RW>
-__device__ __forceinline__ void fill_up(const uint32_t (&Q)[RW], const uint32_t (&X)[RW], uint32_t (&F)[RW]) {
-  unsigned long long c = 0;
-#pragma unroll
-  for (int m = 0; m < RW; ++m) {
-    const unsigned long long sum = (unsigned long long)Q[m] + X[m] + c;
-    c = sum >> 32;
-    F[m] = (((uint32_t)sum ^ Q[m]) & Q[m]) | X[m];
-  }
-}
-
-// Reverse the L0-bit string held in RW words (bit x -> bit L0-1-x).
-template <int RW>
-__device__ __forceinline__ void reverse_row(const uint32_t (&A)[RW], uint32_t (&B)[RW], int L0) {
-  uint32_t t[RW];
-#pragma unroll
-  for (int m = 0; m < RW; ++m) t[m] = __brev(A[RW - 1 - m]);
-  const int sh = 32 * RW - L0; // 0..31
-  if (sh == 0) {
-#pragma unroll
-    for (int m = 0; m < RW; ++m) B[m] = t[m];
-  } else {
-#pragma unroll
-    for (int m = 0; m < RW; ++m) {
-      const uint32_t hi = m + 1 < RW ? t[m + 1] : 0u;
-      B[m] = (t[m] >> sh) | (hi << (32 - sh));
-    }
-  }
-}
-
-template <int RW>
-__device__ __forceinline__ void fill_down(const uint32_t (&Q)[RW], const uint32_t (&X)[RW], uint32_t (&F)[RW],
-                                          int L0) {
-  uint32_t rq[RW], rx[RW], rf[RW];
-  reverse_row<RW>(Q, rq, L0);
-  reverse_row<RW>(X, rx, L0);
-  fill_up<RW>(rq, rx, rf);
-  reverse_row<RW>(rf, F, L0);
-}
-
-// F = the union of the runs of the periodic L0-bit row Q that contain a bit of X.
-template <int RW>
-__device__ __forceinline__ void close_row(const uint32_t (&Q)[RW], const uint32_t (&X)[RW], uint32_t (&F)[RW],
-                                          int L0) {
-  uint32_t a[RW], b[RW];
-  fill_up<RW>(Q, X, a);
-  fill_down<RW>(Q, X, b, L0);
-#pragma unroll
-  for (int m = 0; m < RW; ++m) F[m] = a[m] | b[m];
-  // periodic wrap: a run through x = L0-1 continues at x = 0 and vice versa
-  const int tw = (L0 - 1) >> 5, tb = (L0 - 1) & 31;
-  uint32_t ftop = 0u, qtopw = 0u;
-#pragma unroll
-  for (int m = 0; m < RW; ++m)
-    if (m == tw) {
-      ftop = F[m];
-      qtopw = Q[m];
-    }
-  const bool top_in = (ftop >> tb) & 1u, bot_in = F[0] & 1u;
-  const bool qtop = (qtopw >> tb) & 1u, qbot = Q[0] & 1u;
-  if (top_in && qbot && !bot_in) {
-    uint32_t s[RW], g[RW];
-#pragma unroll
-    for (int m = 0; m < RW; ++m) s[m] = m == 0 ? 1u : 0u;
-    fill_up<RW>(Q, s, g);
-#pragma unroll
-    for (int m = 0; m < RW; ++m) F[m] |= g[m];
-  }
-  uint32_t ftop2 = 0u;
-#pragma unroll
-  for (int m = 0; m < RW; ++m)
-    if (m == tw) ftop2 = F[m];
-  if (bot_in && qtop && !((ftop2 >> tb) & 1u)) {
-    uint32_t s[RW], g[RW];
-#pragma unroll
-    for (int m = 0; m < RW; ++m) s[m] = m == tw ? (1u << tb) : 0u;
-    fill_down<RW>(Q, s, g, L0);
-#pragma unroll
-    for (int m = 0; m < RW; ++m) F[m] |= g[m];
-  }
-}
 
 // Canonical site of bitmap block b, lane l (row r = b / RW, x = 32 (b % RW) + l) as a
 // colour-split index p; `valid` is false for the padding bits past L0.
@@ -417,18 +332,8 @@ __global__ void __launch_bounds__(HNT) k_houdayer(Job jb, Dev dv, HoudArgs ha) {
 // CTAs of a few pairs, all pairs of all samples in flight together, and the flips are
 // applied by one CTA per sample.
 // ---------------------------------------------------------------------------------
-struct HoudSplit {
-  int RW;        // words per bitmap row
-  int NBW;       // words per bitmap
-  uint32_t *Qg;  // [S][T][NBW] q bitmaps
-  uint32_t *Cg;  // [S][T][NBW] cluster bitmaps
-  uint32_t *Mg;  // [S][32] q = -1 sites per pair (by chain-0 lane)
-  int wpb;       // pairs (warps) per CTA of the fill kernel
-  int in_smem;   // 1: a fill warp copies its bitmaps into shared memory
-};
 constexpr int HSPLIT_NT = 512;     // threads of the per-sample kernels
 constexpr int HFILL_MAX_WARPS = 8; // pairs per CTA of the fill kernel, at most
-constexpr int HFILL_HEAD = 16;     // fill kernel's shared-memory header (two counters)
 
 // The per-sample kernels move the bitmaps between registers and global scratch through a
 // shared-memory tile of HQ_TB blocks for every pair (row stride HQ_TB + 1: the lanes of a
@@ -925,8 +830,8 @@ int houdayer_smem(const Job &jb, int bitmaps_smem) {
 
 size_t houdayer_scratch_bytes(const Job &jb) {
   const int RW = (jb.g.L0 + 31) / 32;
-  // q and cluster bitmaps of every pair, then M per (sample, lane)
-  return (size_t)jb.S * 2 * jb.T * (size_t)(jb.g.R * RW) * 4 + (size_t)jb.S * 32 * 4;
+  // q and cluster bitmaps of every pair, then M per (sample, lane), then the pair queue
+  return (size_t)jb.S * 2 * jb.T * (size_t)(jb.g.R * RW) * 4 + (size_t)jb.S * 32 * 4 + 16;
 }
 
 namespace {
@@ -1013,7 +918,7 @@ cudaError_t prepare_houdayer_kernels(int max_smem) {
       }
     }
   }
-  return cudaSuccess;
+  return prepare_houd_seed_kernels(max_smem);
 }
 
 bool houdayer_labels(const Job &jb) {
@@ -1034,6 +939,7 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     hs.Qg = scratch;
     hs.Cg = scratch + (size_t)jb.S * jb.T * NBW;
     hs.Mg = hs.Cg + (size_t)jb.S * jb.T * NBW;
+    hs.queue = hs.Mg + (size_t)jb.S * 32;
     int smem = 0;
     fill_shape(jb, NBW, &hs.wpb, &hs.in_smem, &smem);
     const long long pairs = (long long)jb.S * jb.T;
@@ -1045,11 +951,18 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     parts = parts < 1 ? 1 : (parts > 8 ? 8 : parts);
     parts = parts > tiles ? tiles : parts;
     const dim3 pgrid((unsigned)jb.S, (unsigned)parts);
-    cudaError_t e0 = cudaMemsetAsync(hs.Mg, 0, (size_t)jb.S * 32 * 4, st);
+    cudaError_t e0 = cudaMemsetAsync(hs.Mg, 0, (size_t)jb.S * 32 * 4 + 16, st); // M and the pair queue
     if (e0 != cudaSuccess) return e0;
     k_houd_q<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     const int lab = label_smem_bytes(NBW, jb.g.N, jb.g.R, jb.g.d);
-    if (houdayer_labels(jb)) {
+    // the single-cluster move grows only the seed's cluster where a fill form applies
+    bool seeded = false;
+    if (!multi) {
+      const cudaError_t es = launch_houd_seed(jb, dv, hs, n_sm, st, &seeded);
+      if (es != cudaSuccess) return es;
+    }
+    if (seeded) {
+    } else if (houdayer_labels(jb)) {
       pick_label(jb.g.d, RW, multi)<<<(unsigned)pairs, HLAB_NT, (size_t)lab, st>>>(jb, dv, hs);
     } else {
       if (multi) return cudaErrorNotSupported;

@@ -120,12 +120,21 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__re
 // x - exp(delta) >= 2.5e-11, so both fast outcomes agree with the fp64 test and are
 // never within the 1e-12 near-threshold window, whatever the last-bit errors of exp and
 // the products.
+//
+// The pass: at step k the pair is (replica now at slot k, replica at slot k+1), and the
+// replica at slot k+1 is still the one from before the pass.  So the replica that may keep
+// climbing and its energy are carried in registers, and the other operands of step k
+// (the replica at slot k+1, its energy, the bounds of pair k) come from the lanes that
+// hold them by shuffles that do not depend on earlier decisions.  Every lane runs the pass
+// (same values, same branches); lane k % 32 keeps the replica that ends at slot k.
+// pacc, pnear and pexact accumulate; pm and sl are rewritten at the end.
 __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, int32_t *pm, int32_t *sl,
-                                                    const int32_t *el, int32_t *accb, int32_t *rejb,
-                                                    uint32_t *uw, unsigned int *pacc, unsigned int *pnear,
-                                                    unsigned int *pexact, uint32_t *slowmask, uint32_t s_glob,
-                                                    uint32_t c, uint32_t t, const Job &jb) {
+                                                    const int32_t *el, unsigned int *pacc, unsigned int *pnear,
+                                                    unsigned int *pexact, uint32_t s_glob, uint32_t c, uint32_t t,
+                                                    const Job &jb) {
   const int lane = threadIdx.x & 31;
+  int Ar[2] = {0, 0}, Rr[2] = {0, 0};
+  uint32_t ur[2] = {0u, 0u}, slowm[2] = {0u, 0u};
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int k = lane + 32 * half;
@@ -134,7 +143,6 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
       const uint32_t u = philox10_rk((uint32_t)k, t, s_glob, (c << 20) | TAG_PT, jb.rk0, jb.rk1).x;
       const float dbeta = (float)__dsub_rn(beta[k], beta[k + 1]);
       slow = (u == 0u);
-      int A = 0, R = 0;
       if (!slow) {
         // bounds in fp32: ln x to ~3e-7 relative (log1p near x = 1, where 1 - x is exact),
         // dbeta to 6e-8, so theta is within 5e-7 |theta| and the margin covers it 8 times
@@ -147,48 +155,78 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
         if (!(hi == hi) || !(lo == lo)) {
           slow = true;
         } else {
-          A = hi >= LIM ? (int)LIM : (hi <= -LIM ? -(int)LIM : (int)ceilf(hi));
-          R = lo <= -LIM ? -(int)LIM : (lo >= LIM ? (int)LIM : (int)floorf(lo));
+          Ar[half] = hi >= LIM ? (int)LIM : (hi <= -LIM ? -(int)LIM : (int)ceilf(hi));
+          Rr[half] = lo <= -LIM ? -(int)LIM : (lo >= LIM ? (int)LIM : (int)floorf(lo));
         }
       }
-      accb[k] = A;
-      rejb[k] = R;
-      uw[k] = u;
+      ur[half] = u;
     }
-    const uint32_t sm = __ballot_sync(FULL, slow);
-    if (lane == 0) slowmask[half] = sm;
+    slowm[half] = __ballot_sync(FULL, slow);
+  }
+  const int p0 = lane < T ? pm[lane] : 0, p1 = lane + 32 < T ? pm[lane + 32] : 0;
+  const int e0 = lane < T ? el[p0] : 0, e1 = lane + 32 < T ? el[p1] : 0;
+  int np0 = p0, np1 = p1;
+  uint32_t acc0 = 0u, acc1 = 0u;
+  unsigned int n_exact = 0u, n_near = 0u;
+  int cur = __shfl_sync(FULL, p0, 0), ecur = __shfl_sync(FULL, e0, 0);
+  for (int k = 0; k + 1 < T; ++k) {
+    const int kn = k + 1;
+    const bool lo_n = kn < 32, lo_k = k < 32; // warp-uniform
+    const int b = __shfl_sync(FULL, lo_n ? p0 : p1, kn & 31);
+    const int eb = __shfl_sync(FULL, lo_n ? e0 : e1, kn & 31);
+    const int Ak = __shfl_sync(FULL, lo_k ? Ar[0] : Ar[1], k & 31);
+    const int Rk = __shfl_sync(FULL, lo_k ? Rr[0] : Rr[1], k & 31);
+    const bool slow = (((lo_k ? slowm[0] : slowm[1]) >> (k & 31)) & 1u) != 0u;
+    const int dE = ecur - eb;
+    bool accept;
+    if (dE >= 0) {
+      accept = true;
+    } else if (!slow && dE >= Ak) {
+      accept = true;
+    } else if (!slow && dE <= Rk) {
+      accept = false;
+    } else {
+      const uint32_t uk = __shfl_sync(FULL, lo_k ? ur[0] : ur[1], k & 31);
+      const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
+      const double delta = __dmul_rn(dbeta, (double)dE);
+      const double x = __dmul_rn((double)uk, 0x1p-32);
+      const double e = exp(delta);
+      if (fabs(__dsub_rn(x, e)) < 1e-12) ++n_near;
+      ++n_exact;
+      accept = x < e;
+    }
+    const int placed = accept ? b : cur; // the replica that ends the pass at slot k
+    if (!accept) {
+      cur = b;
+      ecur = eb;
+    }
+    if (lane == (k & 31)) {
+      if (lo_k) np0 = placed;
+      else np1 = placed;
+    }
+    if (accept) {
+      if (lo_k) acc0 |= 1u << k;
+      else acc1 |= 1u << (k - 32);
+    }
+  }
+  if (T >= 1 && lane == ((T - 1) & 31)) {
+    if (T - 1 < 32) np0 = cur;
+    else np1 = cur;
   }
   __syncwarp();
+  if (lane < T) {
+    pm[lane] = np0;
+    sl[np0] = lane;
+  }
+  if (lane + 32 < T) {
+    pm[lane + 32] = np1;
+    sl[np1] = lane + 32;
+  }
+  if ((acc0 >> lane) & 1u) pacc[lane] += 1u;
+  if ((acc1 >> lane) & 1u) pacc[lane + 32] += 1u;
   if (lane == 0) {
-    const uint32_t slow0 = slowmask[0], slow1 = slowmask[1];
-    for (int k = 0; k + 1 < T; ++k) {
-      const int a = pm[k], b = pm[k + 1];
-      const int dE = el[a] - el[b];
-      const bool slow = ((k < 32 ? (slow0 >> k) : (slow1 >> (k - 32))) & 1u) != 0u;
-      bool accept;
-      if (dE >= 0) {
-        accept = true;
-      } else if (!slow && dE >= accb[k]) {
-        accept = true;
-      } else if (!slow && dE <= rejb[k]) {
-        accept = false;
-      } else {
-        const double dbeta = __dsub_rn(beta[k], beta[k + 1]);
-        const double delta = __dmul_rn(dbeta, (double)dE);
-        const double x = __dmul_rn((double)uw[k], 0x1p-32);
-        const double e = exp(delta);
-        if (fabs(__dsub_rn(x, e)) < 1e-12) *pnear += 1u;
-        *pexact += 1u;
-        accept = x < e;
-      }
-      if (accept) {
-        pacc[k] += 1u;
-        pm[k] = b;
-        pm[k + 1] = a;
-        sl[a] = k + 1;
-        sl[b] = k;
-      }
-    }
+    *pnear += n_near;
+    *pexact += n_exact;
   }
   __syncwarp();
 }
@@ -221,21 +259,18 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   int32_t *epart = reinterpret_cast<int32_t *>(smem + L.epart);
   int32_t *ptw = reinterpret_cast<int32_t *>(smem + L.pt);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-  // per chain slot ci: pm, sl, el, pacc, accb, rejb, uw [64 each], then near and slow mask
+  // per chain slot ci: pm, sl, el, pacc [64 each], near and exact-path counts, round-trip
+  // direction and start [64 each], trips and their total
   auto PM = [&](int ci) { return ptw + ci * PT_WORDS; };
   auto SL = [&](int ci) { return ptw + ci * PT_WORDS + 64; };
   auto EL = [&](int ci) { return ptw + ci * PT_WORDS + 128; };
   auto PACC = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 192); };
-  auto ACCB = [&](int ci) { return ptw + ci * PT_WORDS + 256; };
-  auto REJB = [&](int ci) { return ptw + ci * PT_WORDS + 320; };
-  auto UW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 384); };
-  auto NEAR = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 448); };
-  auto SLOW = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 449); };
-  auto EXACT = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 451); };
-  auto TD = [&](int ci) { return ptw + ci * PT_WORDS + 452; };
-  auto T0 = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 516); };
-  auto TN = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 580); };
-  auto TSUM = [&](int ci) { return reinterpret_cast<unsigned long long *>(ptw + ci * PT_WORDS + 582); };
+  auto NEAR = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 256); };
+  auto EXACT = [&](int ci) { return reinterpret_cast<unsigned int *>(ptw + ci * PT_WORDS + 257); };
+  auto TD = [&](int ci) { return ptw + ci * PT_WORDS + 258; };
+  auto T0 = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 322); };
+  auto TN = [&](int ci) { return reinterpret_cast<uint32_t *>(ptw + ci * PT_WORDS + 386); };
+  auto TSUM = [&](int ci) { return reinterpret_cast<unsigned long long *>(ptw + ci * PT_WORDS + 388); };
   const bool track = dv.trip_dir != nullptr;
   // energies after a Houdayer move (pad0 = 1): the move conserves E_a + E_b of the pair at
   // each slot, so only chain 0's words are counted and chain 1's energies follow
@@ -362,9 +397,8 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     if (nch > 0) {
       // warp ci exchanges chain ci, then refreshes the tables of the chain's words
       if (warp < nch) {
-        exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), ACCB(warp), REJB(warp), UW(warp),
-                            PACC(warp), NEAR(warp), EXACT(warp), SLOW(warp), s_glob, (uint32_t)(c0 + warp),
-                            t_pt0 + (uint32_t)m, jb);
+        exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), PACC(warp), NEAR(warp), EXACT(warp), s_glob,
+                            (uint32_t)(c0 + warp), t_pt0 + (uint32_t)m, jb);
         if (track) {
           uint32_t n_add = 0u;
           unsigned long long sum_add = 0ull;
@@ -510,7 +544,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   int32_t *sl = reinterpret_cast<int32_t *>(smem + L.sl);
   unsigned int *pacc = reinterpret_cast<unsigned int *>(smem + L.pacc);
   unsigned int *pnear = reinterpret_cast<unsigned int *>(smem + L.near);
-  int32_t *xch = reinterpret_cast<int32_t *>(smem + L.xch); // T <= 64: accb, rejb, uw, slow mask, exact count
+  int32_t *xch = reinterpret_cast<int32_t *>(smem + L.xch); // T <= 64: the warp exchange's exact-path count
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
 
   const int tid = threadIdx.x;
@@ -539,7 +573,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   }
   if (tid == 0) {
     *pnear = 0u;
-    if (T <= 64) xch[194] = 0;
+    if (T <= 64) xch[0] = 0;
   }
   __syncthreads();
   if (!ENERGY_ONLY)
@@ -559,6 +593,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   __syncthreads();
 
   const int H = g.H, L1 = g.L1, Nh = g.Nh;
+  const int n_chunks = G * ((Nh + 31) / 32); // (replica group, 32 sites) items per half-sweep
   const int n_outer = ENERGY_ONLY ? 1 : n_mcs;
   const int n_inner = ENERGY_ONLY ? 1 : n_metro;
   for (int m = 0; m < n_outer; ++m) {
@@ -569,68 +604,78 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
           for (int j = tid; j < Tp; j += NT) eacc[j] = 0;
           __syncthreads();
         }
-        for (int it = tid; it < Nh * G; it += NT) {
-          const int q = it / G;
-          const int gi = it - q * G;
-          const int row = q / H;
-          const int k = q - row * H;
-          const int y = D == 3 ? row % L1 : row;
-          const int z = D == 3 ? row / L1 : 0;
-          const int xodd = col ^ ((y + z) & 1);
-          SiteGeo sg;
-          sg.c = col;
-          sg.row = row;
-          sg.k = k;
-          sg.y = y;
-          sg.z = z;
-          sg.xodd = xodd;
-          const int p = col * Nh + q;
-          const uint32_t jbb = jbyte[p];
-          char4 s4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)p * Tp + 4 * gi);
-          int h[4] = {0, 0, 0, 0};
+        // a warp takes 32 consecutive sites of one replica group at a time, so that its
+        // lanes' energy terms can be summed over the warp before one shared add each
+        for (int ch = tid >> 5; ch < n_chunks; ch += NT / 32) {
+          const int gi = ch % G;
+          const int q = (ch / G) * 32 + (tid & 31);
+          const bool valid = q < Nh;
+          int sv[4] = {0, 0, 0, 0}, h[4] = {0, 0, 0, 0};
+          if (valid) {
+            const int row = q / H;
+            const int k = q - row * H;
+            const int y = D == 3 ? row % L1 : row;
+            const int z = D == 3 ? row / L1 : 0;
+            const int xodd = col ^ ((y + z) & 1);
+            SiteGeo sg;
+            sg.c = col;
+            sg.row = row;
+            sg.k = k;
+            sg.y = y;
+            sg.z = z;
+            sg.xodd = xodd;
+            const int p = col * Nh + q;
+            const uint32_t jbb = jbyte[p];
+            char4 s4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)p * Tp + 4 * gi);
 #pragma unroll
-          for (int mu = 0; mu < D; ++mu) {
+            for (int mu = 0; mu < D; ++mu) {
 #pragma unroll
-            for (int dir = 0; dir < 2; ++dir) {
-              const int pn = nbr_cs(g, sg, mu, dir == 0 ? 1 : -1);
-              const char4 n4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)pn * Tp + 4 * gi);
-              const int Jv = ((jbb >> (2 * mu + dir)) & 1u) ? -1 : 1;
-              h[0] += Jv * n4.x;
-              h[1] += Jv * n4.y;
-              h[2] += Jv * n4.z;
-              h[3] += Jv * n4.w;
-            }
-          }
-          int sv[4] = {s4.x, s4.y, s4.z, s4.w};
-          if (!ENERGY_ONLY) {
-            int dE[4];
-            bool need = false;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              dE[r] = 2 * sv[r] * h[r];
-              need |= (4 * gi + r < T) && dE[r] > 0;
-            }
-            uint4 rnd = make_uint4(0, 0, 0, 0);
-            if (need) {
-              const uint32_t i = (uint32_t)(g.L0 * row + 2 * k + xodd);
-              rnd = philox10(i, t, s_glob, ((uint32_t)c << 20) | ((uint32_t)gi << 8) | TAG_METRO, jb.sk0,
-                             jb.sk1);
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int j = 4 * gi + r;
-              if (j < T) {
-                const bool acc = dE[r] <= 0 || word_of(rnd, r) < thr[j * 4 + (dE[r] >> 2)];
-                if (acc) sv[r] = -sv[r];
+              for (int dir = 0; dir < 2; ++dir) {
+                const int pn = nbr_cs(g, sg, mu, dir == 0 ? 1 : -1);
+                const char4 n4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)pn * Tp + 4 * gi);
+                const int Jv = ((jbb >> (2 * mu + dir)) & 1u) ? -1 : 1;
+                h[0] += Jv * n4.x;
+                h[1] += Jv * n4.y;
+                h[2] += Jv * n4.z;
+                h[3] += Jv * n4.w;
               }
             }
-            s4 = make_char4((signed char)sv[0], (signed char)sv[1], (signed char)sv[2], (signed char)sv[3]);
-            *reinterpret_cast<char4 *>(sp8 + (size_t)p * Tp + 4 * gi) = s4;
+            sv[0] = s4.x;
+            sv[1] = s4.y;
+            sv[2] = s4.z;
+            sv[3] = s4.w;
+            if (!ENERGY_ONLY) {
+              int dE[4];
+              bool need = false;
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                dE[r] = 2 * sv[r] * h[r];
+                need |= (4 * gi + r < T) && dE[r] > 0;
+              }
+              uint4 rnd = make_uint4(0, 0, 0, 0);
+              if (need) {
+                const uint32_t i = (uint32_t)(g.L0 * row + 2 * k + xodd);
+                rnd = philox10(i, t, s_glob, ((uint32_t)c << 20) | ((uint32_t)gi << 8) | TAG_METRO, jb.sk0,
+                               jb.sk1);
+              }
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const int j = 4 * gi + r;
+                if (j < T) {
+                  const bool acc = dE[r] <= 0 || word_of(rnd, r) < thr[j * 4 + (dE[r] >> 2)];
+                  if (acc) sv[r] = -sv[r];
+                }
+              }
+              s4 = make_char4((signed char)sv[0], (signed char)sv[1], (signed char)sv[2], (signed char)sv[3]);
+              *reinterpret_cast<char4 *>(sp8 + (size_t)p * Tp + 4 * gi) = s4;
+            }
           }
           if (col == 1) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-              if (4 * gi + r < T) atomicAdd(&eacc[4 * gi + r], -sv[r] * h[r]);
+            for (int r = 0; r < 4; ++r) {
+              const int e = __reduce_add_sync(FULL, -sv[r] * h[r]);
+              if ((tid & 31) == 0 && 4 * gi + r < T && e) atomicAdd(&eacc[4 * gi + r], e);
+            }
           }
         }
         __syncthreads();
@@ -639,9 +684,8 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
     if (FUSE_PT) {
       if (T <= 64) { // one warp: integer bounds first, the exact fp64 test only near them
         if (tid < 32) {
-          exchange_chain_smem(T, dv.beta, pm, sl, eacc, xch, xch + 64, reinterpret_cast<uint32_t *>(xch + 128), pacc,
-                              pnear, reinterpret_cast<unsigned int *>(xch + 194),
-                              reinterpret_cast<uint32_t *>(xch + 192), s_glob, (uint32_t)c, t_pt0 + (uint32_t)m, jb);
+          exchange_chain_smem(T, dv.beta, pm, sl, eacc, pacc, pnear, reinterpret_cast<unsigned int *>(xch), s_glob,
+                              (uint32_t)c, t_pt0 + (uint32_t)m, jb);
           if (tid == 0) trip_chain(dv, (size_t)s * jb.C + c, T, sl, t_pt0 + (uint32_t)m + 1u);
         }
       } else if (tid == 0) {
@@ -667,7 +711,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
     }
   }
   if (FUSE_PT && tid == 0 && *pnear) atomicAdd(&dv.ctr[CTR_NEAR], (unsigned long long)*pnear);
-  if (FUSE_PT && T <= 64 && tid == 0 && xch[194]) atomicAdd(&dv.ctr[CTR_XEXACT], (unsigned long long)xch[194]);
+  if (FUSE_PT && T <= 64 && tid == 0 && xch[0]) atomicAdd(&dv.ctr[CTR_XEXACT], (unsigned long long)xch[0]);
   if (!ENERGY_ONLY) {
     fence_proxy_async();
     __syncthreads();
@@ -697,7 +741,8 @@ namespace {
 typedef void (*int8_fn)(Job, Dev, int, int);
 
 template <bool FUSE, bool EONLY>
-int8_fn pick_int8(int d) {
+int8_fn pick_int8(int d, int nt) {
+  if (nt == 512) return d == 2 ? k_resident_int8<2, 512, FUSE, EONLY> : k_resident_int8<3, 512, FUSE, EONLY>;
   return d == 2 ? k_resident_int8<2, 256, FUSE, EONLY> : k_resident_int8<3, 256, FUSE, EONLY>;
 }
 
@@ -707,6 +752,7 @@ using packed_fn = void (*)(ResidentParams<MAXJ>);
 template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false>
 packed_fn<MAXJ> pick_packed_nt(int nt) {
   switch (nt) {
+  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS>;
   case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS>;
   case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS>;
   case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS>;
@@ -729,12 +775,15 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
                             int32_t *meas_E, int32_t *meas_Q, bool after_move) {
   if (int8fmt) {
+    // small chains: enough threads that a half-sweep is one pass of (group, 32 sites) items
+    const int chunks = (jb.Tp / 4) * ((jb.g.Nh + 31) / 32);
+    const int nt = chunks > 8 && chunks <= 16 ? 512 : 256;
     int8_fn fn;
-    if (energy_only && fuse_pt) fn = pick_int8<true, true>(jb.g.d);
-    else if (energy_only) fn = pick_int8<false, true>(jb.g.d);
-    else if (fuse_pt) fn = pick_int8<true, false>(jb.g.d);
-    else fn = pick_int8<false, false>(jb.g.d);
-    fn<<<(unsigned)(jb.S * jb.C), 256, smem, st>>>(jb, dv, n_mcs, n_metro);
+    if (energy_only && fuse_pt) fn = pick_int8<true, true>(jb.g.d, nt);
+    else if (energy_only) fn = pick_int8<false, true>(jb.g.d, nt);
+    else if (fuse_pt) fn = pick_int8<true, false>(jb.g.d, nt);
+    else fn = pick_int8<false, false>(jb.g.d, nt);
+    fn<<<(unsigned)(jb.S * jb.C), (unsigned)nt, smem, st>>>(jb, dv, n_mcs, n_metro);
     return cudaGetLastError();
   }
   ResidentParams<1> rp;
@@ -790,19 +839,20 @@ cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int w
 cudaError_t prepare_resident_kernels(int max_smem) {
   std::vector<const void *> fns;
   for (int d = 2; d <= 3; ++d)
-    for (int nt : {128, 256, 512, 1024})
+    for (int nt : {64, 128, 256, 512, 1024})
       for (int wpc = 1; wpc <= 2; ++wpc) {
         fns.push_back((const void *)pick_packed<false, 1>(d, nt, wpc));
         fns.push_back((const void *)pick_packed<true, 1>(d, nt, wpc));
         fns.push_back((const void *)pick_packed<false, MAX_BATCH_JOBS>(d, nt, wpc));
         if (wpc == 2) fns.push_back((const void *)pick_packed_meas(d, nt));
       }
-  for (int d = 2; d <= 3; ++d) {
-    fns.push_back((const void *)pick_int8<false, false>(d));
-    fns.push_back((const void *)pick_int8<true, false>(d));
-    fns.push_back((const void *)pick_int8<false, true>(d));
-    fns.push_back((const void *)pick_int8<true, true>(d));
-  }
+  for (int d = 2; d <= 3; ++d)
+    for (int nt : {256, 512}) {
+      fns.push_back((const void *)pick_int8<false, false>(d, nt));
+      fns.push_back((const void *)pick_int8<true, false>(d, nt));
+      fns.push_back((const void *)pick_int8<false, true>(d, nt));
+      fns.push_back((const void *)pick_int8<true, true>(d, nt));
+    }
   for (const void *fn : fns) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;

@@ -218,7 +218,7 @@ cudaError_t prepare_device() {
 // the sample's words, and the lattice must fit in shared memory.
 bool packed_shape_ok(const sg_handle *h, int nt, int wpc, int smem_limit, size_t *smem) {
   const Geo &g = h->job.g;
-  if (nt != 128 && nt != 256 && nt != 512 && nt != 1024) return false;
+  if (nt != 64 && nt != 128 && nt != 256 && nt != 512 && nt != 1024) return false;
   if (wpc != 1 && wpc != 2) return false;
   if (h->job.W % wpc) return false;
   const int per_thread = (g.Nh + nt - 1) / nt;

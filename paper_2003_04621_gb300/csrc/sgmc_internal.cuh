@@ -371,9 +371,10 @@ __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 // Shared-memory map of the resident packed kernel: `wpc` 32-replica word lattices of one
 // sample, its expanded couplings, per-lane threshold tables, energy partial sums and the
 // per-chain exchange scratch.
-// per chain (<= 64 replicas): perm, slot, E, accepts, bounds, u; near-threshold count,
-// slow-flag masks and exact-path count; round-trip state (direction, start) and counters
-constexpr int PT_WORDS = 9 * 64 + 8;
+// per chain (<= 64 replicas): perm, slot, E, accepts; near-threshold and exact-path
+// counts; round-trip state (direction, start) and counters (an even count of words, so
+// that each chain's 64-bit trip total stays 8-byte aligned)
+constexpr int PT_WORDS = 6 * 64 + 8;
 struct PackedSmem {
   int spin, jbyte, jpl, thr, epart, pt, bar, total;
 };
@@ -405,8 +406,8 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
   L.sl = L.pm + round16(4 * T);
   L.pacc = L.sl + round16(4 * T);
   L.near = L.pacc + round16(4 * T);
-  L.xch = L.near + 16; // warp exchange scratch (T <= 64): bounds and words [3][64], flags [2], exact count
-  L.bar = L.xch + (T <= 64 ? round16(4 * (3 * 64 + 4)) : 0);
+  L.xch = L.near + 16; // warp exchange (T <= 64): its exact-path count
+  L.bar = L.xch + 16;
   L.total = L.bar + 16;
   return L;
 }

@@ -263,7 +263,8 @@ def test_status_codes_on_device():
         L.sg_destroy(hb)
 
 
-@pytest.mark.parametrize("ndim,dims,T", [(3, (16, 16, 16), 32), (2, (32, 48), 24), (3, (6, 8, 4), 40)])
+@pytest.mark.parametrize("ndim,dims,T", [(3, (16, 16, 16), 32), (2, (32, 48), 24), (3, (6, 8, 4), 40),
+                                         (3, (8, 8, 8), 20)])
 def test_every_launch_shape_gives_identical_results(oracle_mod, ndim, dims, T):
     """The resident kernel's CTA size and words per CTA are tuning knobs only."""
     kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.5, 2.0, T), sim_seed=3)
@@ -272,7 +273,7 @@ def test_every_launch_shape_gives_identical_results(oracle_mod, ndim, dims, T):
     ran = 0
     from paper_2003_04621_gb300.sgmc import SGError
 
-    for nt in (128, 256, 512, 1024):
+    for nt in (64, 128, 256, 512, 1024):
         for words in (1, 2):
             sim = gpu_of(**kw)
             try:

@@ -2,7 +2,8 @@
 
 The Markov chain of Sec. 2.2/2.4 (Metropolis sweeps, replica exchange by Eq. 5,
 Houdayer moves by Eq. 10) must sample the Boltzmann distribution.  On lattices small
-enough to enumerate all 2^N states (2D 4x4, 3D 2x2x4 and 2x2x2), the oracle's
+enough to enumerate all 2^N states (2D 4x4, 3D 2x2x4, 2x2x2 and 2x2x3, the last in the
+sequential typewriter order since an odd extent has no checkerboard), the oracle's
 time averages of E and of the specific heat C = beta^2 (<E^2> - <E>^2) / N must agree
 with the exact values within their statistical errors (bins of consecutive MCS,
 jackknife for C).  The replica-exchange acceptance per pair must equal its exact
@@ -73,12 +74,17 @@ CASES = [
     # the multi-cluster variant of the move (houdayer = 2)
     ("2d4x4_pt_multicluster", 2, (4, 4), [0.5, 0.8, 1.2, 1.8], 120_000, 2, True),
     ("3d2x2x4_pt_multicluster", 3, (2, 2, 4), [0.8, 1.2, 1.8, 2.6], 120_000, 2, True),
+    # an odd extent: sequential (typewriter) sweeps
+    ("3d2x2x3_metropolis_typewriter", 3, (2, 2, 3), [0.6, 1.0, 1.6, 2.4], 120_000, False, False),
+    ("3d2x2x3_pt_typewriter", 3, (2, 2, 3), [0.6, 1.0, 1.6, 2.4], 120_000, False, True),
+    ("3d2x2x3_pt_houdayer_typewriter", 3, (2, 2, 3), [0.6, 1.0, 1.6, 2.4], 120_000, True, True),
 ]
 
 
 @pytest.mark.parametrize("label,ndim,dims,temps,n_mcs,houd,pt", CASES, ids=[c[0] for c in CASES])
 def test_mc_averages_match_enumeration(oracle_mod, label, ndim, dims, temps, n_mcs, houd, pt):
-    o = oracle_mod.Oracle(oracle_mod.OracleParams(ndim, dims, 1, 2, temps, coupling_seed=1, sim_seed=5))
+    o = oracle_mod.Oracle(oracle_mod.OracleParams(ndim, dims, 1, 2, temps, coupling_seed=1, sim_seed=5,
+                                                  typewriter=any(L % 2 for L in dims)))
     hist = o.enumerate(0)
     o.mcs(2000, houdayer=houd)  # equilibrate (not measured)
     sE, sE2 = o.run_binned(n_mcs, 60, houdayer=houd, pt=pt)
@@ -155,3 +161,19 @@ def test_low_temperature_houdayer_matches_enumeration(oracle_mod):
     assert o.check_energies() == 0
     c = o.counters()
     assert c["error"] == 0 and c["near_threshold"] == 0
+
+
+def test_typewriter_order_is_sequential(oracle_mod):
+    """The typewriter order is another update order, not another random stream: from the
+    same hot start on an even lattice it reaches a different state than the checkerboard
+    (a site sees its same-sweep predecessors' flips), each order is a deterministic
+    function of the counters (two runs agree), and both keep the energies exact."""
+    kw = dict(ndim=3, dims=(2, 2, 4), n_samples=1, n_chains=1, temps=[0.7, 1.3], coupling_seed=2, sim_seed=3)
+    a = oracle_mod.Oracle(oracle_mod.OracleParams(**kw, typewriter=True))
+    b = oracle_mod.Oracle(oracle_mod.OracleParams(**kw, typewriter=True))
+    c = oracle_mod.Oracle(oracle_mod.OracleParams(**kw))
+    for o in (a, b, c):
+        o.sweep(3)
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    assert not np.array_equal(a.spins(), c.spins())
+    assert a.check_energies() == 0 and c.check_energies() == 0
