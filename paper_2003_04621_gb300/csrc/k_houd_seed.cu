@@ -65,13 +65,10 @@ __device__ __forceinline__ uint32_t seed_index(const Job &jb, const Dev &dv, int
 // ---------------------------------------------------------------------------------
 template <int D, int RW, int RPL>
 __global__ void __launch_bounds__(HSEED_NT) k_houd_seedreg(Job jb, Dev dv, HoudSplit hs) {
-  __shared__ unsigned long long cnts[2];
   const int lane = threadIdx.x & 31;
   const Geo g = jb.g;
   const int NBW = hs.NBW;
   const long long pairs = (long long)jb.S * jb.T;
-  if (threadIdx.x < 2) cnts[threadIdx.x] = 0ull;
-  __syncthreads();
   const int bpp = g.L1 / RPL;       // blocks per plane
   const bool owns = lane * RPL < g.R; // lanes past the last row hold empty rows
   const int b = lane % bpp, zb = lane / bpp;
@@ -182,14 +179,10 @@ __global__ void __launch_bounds__(HSEED_NT) k_houd_seedreg(Job jb, Dev dv, HoudS
     n_moves += 1ull;
     n_sites += size;
   }
+  // each warp reports on its own once the queue is empty (no wait for the CTA's others)
   if (lane == 0 && n_moves) {
-    atomicAdd(&cnts[0], n_moves);
-    atomicAdd(&cnts[1], n_sites);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (cnts[0]) atomicAdd(&dv.ctr[CTR_HMOVES], cnts[0]);
-    if (cnts[1]) atomicAdd(&dv.ctr[CTR_HSITES], cnts[1]);
+    atomicAdd(&dv.ctr[CTR_HMOVES], n_moves);
+    atomicAdd(&dv.ctr[CTR_HSITES], n_sites);
   }
 }
 

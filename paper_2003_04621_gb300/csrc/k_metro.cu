@@ -524,6 +524,32 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, 0ull);
 }
 
+// A colour-`col` site of the int8 kernel, from its offset q in the colour's half: its
+// canonical index i and the colour-split indices of its 2d neighbours (+e_mu, -e_mu).
+template <int D>
+struct Int8SiteT {
+  uint32_t i;
+  int pn[2 * D];
+};
+template <int D>
+__device__ __forceinline__ Int8SiteT<D> int8_site(const Geo &g, int col, int q) {
+  Int8SiteT<D> r;
+  SiteGeo sg;
+  sg.c = col;
+  sg.row = q / g.H;
+  sg.k = q - sg.row * g.H;
+  sg.y = D == 3 ? sg.row % g.L1 : sg.row;
+  sg.z = D == 3 ? sg.row / g.L1 : 0;
+  sg.xodd = col ^ ((sg.y + sg.z) & 1);
+  r.i = (uint32_t)(g.L0 * sg.row + 2 * sg.k + sg.xodd);
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu) {
+    r.pn[2 * mu] = nbr_cs(g, sg, mu, 1);
+    r.pn[2 * mu + 1] = nbr_cs(g, sg, mu, -1);
+  }
+  return r;
+}
+
 // ---------------------------------------------------------------------------------
 // int8 resident kernel: one CTA owns one chain (sample s, chain c) with all its replicas,
 // spins as int8 +-1 (the paper's layout, replicas of a site adjacent, Sec. 3).  A thread
@@ -538,7 +564,8 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   int8_t *sp8 = reinterpret_cast<int8_t *>(smem + L.spin);
   uint8_t *jbyte = smem + L.jbyte;
   uint32_t *jpl = reinterpret_cast<uint32_t *>(smem + L.jpl);
-  uint32_t *thr = reinterpret_cast<uint32_t *>(smem + L.thr); // [Tp][4], entry m = 1..d
+  uint32_t *thr = reinterpret_cast<uint32_t *>(smem + L.thr); // [Tp][4], entry m = 1..d, by replica
+  uint32_t *thk = reinterpret_cast<uint32_t *>(smem + L.thk); // [T][4], by temperature slot
   int32_t *eacc = reinterpret_cast<int32_t *>(smem + L.eacc);
   int32_t *pm = reinterpret_cast<int32_t *>(smem + L.pm);
   int32_t *sl = reinterpret_cast<int32_t *>(smem + L.sl);
@@ -576,10 +603,13 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
     if (T <= 64) xch[0] = 0;
   }
   __syncthreads();
-  if (!ENERGY_ONLY)
+  if (!ENERGY_ONLY) {
+    if (T <= INT8_THK_MAX)
+      for (int e = tid; e < 4 * T; e += NT) thk[e] = dv.thr[e];
     for (int j = tid; j < Tp; j += NT)
 #pragma unroll
       for (int m = 0; m < 4; ++m) thr[j * 4 + m] = (j < T && m >= 1 && m <= D) ? dv.thr[sl[j] * 4 + m] : 0u;
+  }
   const bool ok = mbar_wait(bar, 0, MBAR_MAX_TRIES);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
@@ -592,13 +622,25 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   expand_couplings<D, NT>(g, jpl, jbyte);
   __syncthreads();
 
-  const int H = g.H, L1 = g.L1, Nh = g.Nh;
+  const int Nh = g.Nh;
   const int n_chunks = G * ((Nh + 31) / 32); // (replica group, 32 sites) items per half-sweep
+  // when every warp holds at most one item per colour (small chains), the items' site
+  // geometry is computed once for the whole launch
+  const bool one_item = n_chunks <= NT / 32;
+  Int8SiteT<D> cache0 = {}, cache1 = {};
+  if (one_item && (tid >> 5) < n_chunks) {
+    const int q = ((tid >> 5) / G) * 32 + (tid & 31);
+    if (q < Nh) {
+      cache0 = int8_site<D>(g, 0, q);
+      cache1 = int8_site<D>(g, 1, q);
+    }
+  }
   const int n_outer = ENERGY_ONLY ? 1 : n_mcs;
   const int n_inner = ENERGY_ONLY ? 1 : n_metro;
   for (int m = 0; m < n_outer; ++m) {
     for (int swp = 0; swp < n_inner; ++swp) {
       const uint32_t t = t_metro0 + (uint32_t)(m * n_metro + swp);
+      const PhiloxSweep P = philox_sweep(s_glob, t, jb);
       for (int col = ENERGY_ONLY ? 1 : 0; col < 2; ++col) {
         if (col == 1) {
           for (int j = tid; j < Tp; j += NT) eacc[j] = 0;
@@ -612,18 +654,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
           const bool valid = q < Nh;
           int sv[4] = {0, 0, 0, 0}, h[4] = {0, 0, 0, 0};
           if (valid) {
-            const int row = q / H;
-            const int k = q - row * H;
-            const int y = D == 3 ? row % L1 : row;
-            const int z = D == 3 ? row / L1 : 0;
-            const int xodd = col ^ ((y + z) & 1);
-            SiteGeo sg;
-            sg.c = col;
-            sg.row = row;
-            sg.k = k;
-            sg.y = y;
-            sg.z = z;
-            sg.xodd = xodd;
+            const Int8SiteT<D> sn = one_item ? (col ? cache1 : cache0) : int8_site<D>(g, col, q);
             const int p = col * Nh + q;
             const uint32_t jbb = jbyte[p];
             char4 s4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)p * Tp + 4 * gi);
@@ -631,7 +662,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
             for (int mu = 0; mu < D; ++mu) {
 #pragma unroll
               for (int dir = 0; dir < 2; ++dir) {
-                const int pn = nbr_cs(g, sg, mu, dir == 0 ? 1 : -1);
+                const int pn = sn.pn[2 * mu + dir];
                 const char4 n4 = *reinterpret_cast<const char4 *>(sp8 + (size_t)pn * Tp + 4 * gi);
                 const int Jv = ((jbb >> (2 * mu + dir)) & 1u) ? -1 : 1;
                 h[0] += Jv * n4.x;
@@ -654,9 +685,10 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
               }
               uint4 rnd = make_uint4(0, 0, 0, 0);
               if (need) {
-                const uint32_t i = (uint32_t)(g.L0 * row + 2 * k + xodd);
-                rnd = philox10(i, t, s_glob, ((uint32_t)c << 20) | ((uint32_t)gi << 8) | TAG_METRO, jb.sk0,
-                               jb.sk1);
+                // counter (i, t, s, c << 20 | gi << 8 | METRO), the rounds shared by the sweep
+                // and by the site hoisted as in the packed kernel
+                const PhiloxSite Q = philox_site(P, sn.i, jb);
+                rnd = philox_finish(P, Q, ((uint32_t)c << 20) | ((uint32_t)gi << 8) | TAG_METRO, jb);
               }
 #pragma unroll
               for (int r = 0; r < 4; ++r) {
@@ -697,7 +729,8 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
       if (!ENERGY_ONLY)
         for (int j = tid; j < T; j += NT)
 #pragma unroll
-          for (int mm = 1; mm <= D; ++mm) thr[j * 4 + mm] = dv.thr[sl[j] * 4 + mm];
+          for (int mm = 1; mm <= D; ++mm)
+            thr[j * 4 + mm] = T <= INT8_THK_MAX ? thk[sl[j] * 4 + mm] : dv.thr[sl[j] * 4 + mm];
       __syncthreads();
     }
   }

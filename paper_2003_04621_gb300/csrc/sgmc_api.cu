@@ -1,6 +1,7 @@
 // sgmc_api.cu -- host side of the C-ABI declared in include/sgmc.h: parameter checks,
 // the device-memory layout inside the caller's buffer, the host-computed tables
 // (Metropolis thresholds, inverse temperatures) and the kernel launches.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -637,9 +638,30 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
   b->events.resize((size_t)n_handles + 1, nullptr);
   for (auto &ev : b->events)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  // Each job's branch is captured on a stream of its own whose priority ranks the job by
+  // the work of one of its CTAs (sites x words per CTA, x 2 for a chain split over CTAs
+  // whose exchange runs as a second launch): the graph runs with these node priorities,
+  // so the longest items are placed first and the short ones fill in around them instead
+  // of leaving the long ones to run on alone at the end of every launch.
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_least = prio_greatest = 0;
+  std::vector<double> item_work((size_t)n_handles, 0.0);
+  for (int i = 0; i < n_handles; ++i) {
+    const sg_handle *h = handles[i];
+    const int wpc = h->global ? 1 : h->wpc;
+    item_work[i] = (double)h->job.g.N * wpc * (h->fuse_pt ? 1.0 : 2.0);
+  }
+  std::vector<double> ranked = item_work;
+  std::sort(ranked.begin(), ranked.end());
+  ranked.erase(std::unique(ranked.begin(), ranked.end()), ranked.end());
+  const int levels = prio_least - prio_greatest + 1; // priorities prio_greatest..prio_least
   b->streams.resize((size_t)n_handles, nullptr);
-  for (auto &q : b->streams)
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+  for (int i = 0; i < n_handles && e == cudaSuccess; ++i) {
+    // rank 0 = the most work per item -> the greatest priority (the smallest number)
+    const int rank = (int)(ranked.end() - std::upper_bound(ranked.begin(), ranked.end(), item_work[i]));
+    const int prio = prio_greatest + (rank < levels ? rank : levels - 1);
+    e = cudaStreamCreateWithPriority(&b->streams[i], cudaStreamNonBlocking, prio);
+  }
   if (e != cudaSuccess) {
     destroy_batch(b);
     return SG_ECUDA;
@@ -755,7 +777,7 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
     destroy_batch(b);
     return r != SG_OK ? r : SG_ECUDA;
   }
-  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+  if (cudaGraphInstantiate(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     destroy_batch(b);
     return SG_ECUDA;
   }

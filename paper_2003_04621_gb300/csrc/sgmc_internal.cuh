@@ -391,9 +391,10 @@ __host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthr
   return L;
 }
 
+constexpr int INT8_THK_MAX = 256;
 // Shared-memory map of the resident int8 kernel (one chain, all its replicas).
 struct Int8Smem {
-  int spin, jbyte, jpl, thr, eacc, pm, sl, pacc, near, xch, bar, total;
+  int spin, jbyte, jpl, thr, thk, eacc, pm, sl, pacc, near, xch, bar, total;
 };
 __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int Tp) {
   Int8Smem L;
@@ -401,7 +402,10 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
   L.jbyte = L.spin + round16(N * Tp);
   L.jpl = L.jbyte + round16(N);
   L.thr = L.jpl + round16(4 * d * NW);
-  L.eacc = L.thr + 16 * Tp;
+  // the job's table by slot [T][4] for chains of up to 256 replicas, so that the refresh
+  // after an exchange stays on chip (longer chains refresh from global memory)
+  L.thk = L.thr + 16 * Tp;
+  L.eacc = L.thk + (T <= INT8_THK_MAX ? 16 * T : 0);
   L.pm = L.eacc + round16(4 * Tp);
   L.sl = L.pm + round16(4 * T);
   L.pacc = L.sl + round16(4 * T);
