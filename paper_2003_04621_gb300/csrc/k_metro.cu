@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   expand_couplings<D, NT>(g, jpl, jbyte);
   __syncthreads();
 
+  const bool warp_owned = !ENERGY_ONLY && (nch == 0 || (jb.Wc == 1 && nch == WPC));
   const int n_outer = ENERGY_ONLY ? 1 : n_mcs;
   const int n_inner = ENERGY_ONLY ? 1 : n_metro;
   for (int m = 0; m < n_outer; ++m) {
@@ -382,7 +383,11 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         if (nch > 0) EL(my_ci)[my_j0 + lane] = 2 * U - D * g.N;
         else if (lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = 2 * U - D * g.N;
       }
-      __syncthreads();
+      // when each word is a whole chain, the warp that sums a word's energies is the one
+      // that exchanges its chain, so only its own lanes need to see them; otherwise (a
+      // chain of two words, or the energies after a cluster move) the whole CTA waits
+      if (warp_owned) __syncwarp();
+      else __syncthreads();
       if (conserve) {
         // slot k pairs chain-0 replica a = perm0[k] with chain-1 replica b = perm1[k]; the
         // global energies are still those before the move
