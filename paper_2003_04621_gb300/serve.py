@@ -193,7 +193,9 @@ class Server:
         self.side = self.dev.stream()  # job creation and final measurements
         self.tune = tune
         if max_ctas <= 0:
-            max_ctas = 12 * self.dev.n_sm()
+            # 24 sweep CTAs per SM: about eight waves of the resident kernels, enough that
+            # the device stays full as jobs of different lengths come and go
+            max_ctas = 24 * self.dev.n_sm()
         self.max_ctas = int(max_ctas)
         self.max_inflight = max(1, int(max_inflight))
         self.graph_builds = 0
