@@ -892,7 +892,11 @@ cudaError_t prepare_resident_kernels(int max_smem) {
       fns.push_back((const void *)pick_int8<true, true>(d, nt));
     }
   for (const void *fn : fns) {
-    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    // what a launch may add to the kernel's static shared memory
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -115,3 +115,35 @@ def test_batch_of_one_lattice_many_temperature_counts(oracle_mod):
         orc.mcs(6)
         assert_same_state(sim, orc, f"batched T={len(kw['temps'])} C={kw['n_chains']}")
     b.close()
+
+
+def test_batch_of_more_jobs_than_one_table_equals_jobs_run_alone(oracle_mod):
+    """More jobs of one lattice shape than one launch's job table holds (96), next to
+    jobs of two other sizes: that group's resident launches run in two chunks; every job
+    must equal the same job run alone."""
+    from paper_2003_04621_gb300.sgmc import Batch
+
+    rng = np.random.default_rng(5)
+    specs = []
+    for k in range(110):
+        # 100 jobs of one group (L = 6, one word per chain): two chunks of its job table
+        L = 6 if k < 100 else int(rng.choice([4, 8]))
+        T = int(rng.integers(8, 33)) if k < 100 else int(rng.integers(8, 49))
+        specs.append(dict(ndim=3, dims=(L, L, L), n_samples=int(rng.integers(1, 3)), n_chains=2,
+                          temps=geometric_temps(0.9, 2.0, T), sim_seed=11, coupling_seed=k + 1, sample_offset=k))
+    batched = [gpu_of(**kw) for kw in specs]
+    alone = [gpu_of(**kw) for kw in specs]
+    b = Batch(batched, mcs_per_launch=3)
+    b.run(2)
+    for a in alone:
+        a.run_mcs(6)
+    for kw, a, s in zip(specs, alone, batched):
+        assert (a.spins() == s.spins()).all(), kw
+        np.testing.assert_array_equal(a.state()[0], s.state()[0])
+        np.testing.assert_array_equal(a.state()[1], s.state()[1])
+        assert a.state()[2] == s.state()[2]
+    for kw, s in list(zip(specs, batched))[::37]:
+        orc = oracle_of(oracle_mod, **_okw(kw))
+        orc.mcs(6)
+        assert_same_state(s, orc, f"large batch L={kw['dims'][0]} T={len(kw['temps'])}")
+    b.close()
