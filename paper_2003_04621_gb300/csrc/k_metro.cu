@@ -44,10 +44,10 @@ __device__ __forceinline__ void expand_couplings(const Geo &g, const uint32_t *j
 
 // One checkerboard half-sweep over the colour-`col` sites of WPC resident word lattices
 // (all of one sample).  Site geometry, couplings and the site-level Philox parts are
-// shared by the WPC words.  ACCUM adds each site's post-update count to V[w];
-// NOFLIP counts only.
-template <int D, int NT, int WPC, bool ACCUM, bool NOFLIP>
-__device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__restrict__ sp,
+// shared by the WPC words.  `accum` adds each site's post-update count to V[w] (a
+// run-time flag, so that both colours run one copy of the code); NOFLIP counts only.
+template <int D, int NT, int WPC, bool NOFLIP>
+__device__ __forceinline__ void half_sweep(const Geo &g, int col, bool accum, uint32_t *__restrict__ sp,
                                            const uint8_t *__restrict__ jbyte,
                                            const uint2 *__restrict__ pair_tab, const uint32_t *vmask,
                                            const int *ngroups, const uint32_t *c3base, const PhiloxSweep &P,
@@ -97,7 +97,7 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, uint32_t *__re
         F = decide_site<D>(cnt, P, Q, c3base[w], ngroups[w], pair_tab + w * 256, jb) & vmask[w];
         own[q] = s0 ^ F;
       }
-      if (ACCUM) {
+      if (accum) {
         uint32_t v1, v2;
         recount<D>(cnt, F, v1, v2);
         vcount_add(V[w], cnt.u0, v1, v2);
@@ -367,11 +367,17 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
 #pragma unroll
         for (int b = 0; b < NB; ++b) V[w][b] = 0u;
       if (!ENERGY_ONLY) {
-        half_sweep<D, NT, WPC, false, false>(g, 0, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
-        __syncthreads();
+        // colour 0, a barrier, colour 1 with the energy counts: one loop body, one copy of
+        // the half-sweep's code
+#pragma unroll 1
+        for (int col = 0; col < 2; ++col) {
+          half_sweep<D, NT, WPC, false>(g, col, col == 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
+          if (col == 0) __syncthreads();
+        }
+      } else {
+        half_sweep<D, NT, WPC, true>(g, 1, true, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V,
+                                     conserve ? 1 : WPC);
       }
-      half_sweep<D, NT, WPC, true, ENERGY_ONLY>(g, 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V,
-                                                conserve ? 1 : WPC);
 #pragma unroll
       for (int w = 0; w < WPC; ++w) epart[w * NT + tid] = warp_lane_sum(V[w]);
       __syncthreads();
