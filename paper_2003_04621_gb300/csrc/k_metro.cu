@@ -46,7 +46,7 @@ __device__ __forceinline__ void expand_couplings(const Geo &g, const uint32_t *j
 // (all of one sample).  Site geometry, couplings and the site-level Philox parts are
 // shared by the WPC words.  `accum` adds each site's post-update count to V[w] (a
 // run-time flag, so that both colours run one copy of the code); NOFLIP counts only.
-template <int D, int NT, int WPC, bool NOFLIP>
+template <int D, int NT, int WPC, bool NOFLIP, bool FULL>
 __device__ __forceinline__ void half_sweep(const Geo &g, int col, bool accum, uint32_t *__restrict__ sp,
                                            const uint8_t *__restrict__ jbyte,
                                            const uint2 *__restrict__ pair_tab, const uint32_t *vmask,
@@ -94,7 +94,7 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, bool accum, ui
       const SiteCount<D> cnt = count_site<D>(s0, nb, jm);
       uint32_t F = 0;
       if (!NOFLIP) {
-        F = decide_site<D>(cnt, P, Q, c3base[w], ngroups[w], pair_tab + w * 256, jb) & vmask[w];
+        F = decide_site<D, FULL>(cnt, P, Q, c3base[w], ngroups[w], pair_tab + w * 256, jb) & vmask[w];
         own[q] = s0 ^ F;
       }
       if (accum) {
@@ -236,7 +236,9 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
 // n_mcs MCS.  When the job's `fuse` flag is set the item holds whole chains (a chain is
 // Wc <= WPC words) and their exchange passes run between the MCS.  The job comes from a
 // table in parameter space, so one launch can sweep many jobs of one lattice shape.
-template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false>
+// FULL: every word of every job of the launch is full (each chain a multiple of 32
+// replicas), so the partial-word decision code is left out of the instantiation.
+template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false, bool FULL = false>
 __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     k_resident_packed(const __grid_constant__ ResidentParams<MAXJ> rp) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -371,11 +373,11 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         // the half-sweep's code
 #pragma unroll 1
         for (int col = 0; col < 2; ++col) {
-          half_sweep<D, NT, WPC, false>(g, col, col == 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
+          half_sweep<D, NT, WPC, false, FULL>(g, col, col == 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
           if (col == 0) __syncthreads();
         }
       } else {
-        half_sweep<D, NT, WPC, true>(g, 1, true, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V,
+        half_sweep<D, NT, WPC, true, false>(g, 1, true, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V,
                                      conserve ? 1 : WPC);
       }
 #pragma unroll
@@ -793,25 +795,27 @@ int8_fn pick_int8(int d, int nt) {
 template <int MAXJ>
 using packed_fn = void (*)(ResidentParams<MAXJ>);
 
-template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false>
+template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false, bool FULL = false>
 packed_fn<MAXJ> pick_packed_nt(int nt) {
   switch (nt) {
-  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS>;
-  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS>;
-  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS>;
-  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS>;
-  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS>;
+  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS, FULL>;
+  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS, FULL>;
+  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS, FULL>;
+  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS, FULL>;
+  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS, FULL>;
   }
 }
 // the sweep kernel that measures after its last MCS (two one-word chains per CTA)
+template <bool FULL>
 packed_fn<1> pick_packed_meas(int d, int nt) {
-  return d == 2 ? pick_packed_nt<2, 2, false, 1, true>(nt) : pick_packed_nt<3, 2, false, 1, true>(nt);
+  return d == 2 ? pick_packed_nt<2, 2, false, 1, true, FULL>(nt) : pick_packed_nt<3, 2, false, 1, true, FULL>(nt);
 }
 
-template <bool EONLY, int MAXJ>
+template <bool EONLY, int MAXJ, bool FULL = false>
 packed_fn<MAXJ> pick_packed(int d, int nt, int wpc) {
-  if (d == 2) return wpc == 2 ? pick_packed_nt<2, 2, EONLY, MAXJ>(nt) : pick_packed_nt<2, 1, EONLY, MAXJ>(nt);
-  return wpc == 2 ? pick_packed_nt<3, 2, EONLY, MAXJ>(nt) : pick_packed_nt<3, 1, EONLY, MAXJ>(nt);
+  if (d == 2)
+    return wpc == 2 ? pick_packed_nt<2, 2, EONLY, MAXJ, false, FULL>(nt) : pick_packed_nt<2, 1, EONLY, MAXJ, false, FULL>(nt);
+  return wpc == 2 ? pick_packed_nt<3, 2, EONLY, MAXJ, false, FULL>(nt) : pick_packed_nt<3, 1, EONLY, MAXJ, false, FULL>(nt);
 }
 } // namespace
 
@@ -846,8 +850,10 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
   rp.jobs[0].n_items = jb.S * (jb.W / wpc);
   rp.jobs[0].fuse = fuse_pt ? 1 : 0;
   rp.jobs[0].n_metro = n_metro;
-  const packed_fn<1> fn = meas          ? pick_packed_meas(jb.g.d, nthreads)
+  const bool full = jb.T % 32 == 0; // every word of the job is full
+  const packed_fn<1> fn = meas ? (full ? pick_packed_meas<true>(jb.g.d, nthreads) : pick_packed_meas<false>(jb.g.d, nthreads))
                           : energy_only ? pick_packed<true, 1>(jb.g.d, nthreads, wpc)
+                          : full        ? pick_packed<false, 1, true>(jb.g.d, nthreads, wpc)
                                         : pick_packed<false, 1>(jb.g.d, nthreads, wpc);
   fn<<<(unsigned)rp.jobs[0].n_items, nthreads, smem, st>>>(rp);
   return cudaGetLastError();
@@ -886,9 +892,13 @@ cudaError_t prepare_resident_kernels(int max_smem) {
     for (int nt : {64, 128, 256, 512, 1024})
       for (int wpc = 1; wpc <= 2; ++wpc) {
         fns.push_back((const void *)pick_packed<false, 1>(d, nt, wpc));
+        fns.push_back((const void *)pick_packed<false, 1, true>(d, nt, wpc));
         fns.push_back((const void *)pick_packed<true, 1>(d, nt, wpc));
         fns.push_back((const void *)pick_packed<false, MAX_BATCH_JOBS>(d, nt, wpc));
-        if (wpc == 2) fns.push_back((const void *)pick_packed_meas(d, nt));
+        if (wpc == 2) {
+          fns.push_back((const void *)pick_packed_meas<false>(d, nt));
+          fns.push_back((const void *)pick_packed_meas<true>(d, nt));
+        }
       }
   for (int d = 2; d <= 3; ++d)
     for (int nt : {256, 512}) {

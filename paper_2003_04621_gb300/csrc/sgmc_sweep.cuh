@@ -253,40 +253,63 @@ __device__ __forceinline__ uint32_t decide_group(uint32_t rej, const uint4 &r, i
   return rej;
 }
 
-// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.  A full
-// word's eight groups draw their words in one interleaved Philox evaluation, a partial
-// word's two at a time; the reject bits are pushed highest group first.
+// Metropolis decisions of one site's 32 replicas: returns the accepted-flip mask.  The
+// groups of 4 replicas draw their words in interleaved Philox evaluations: a full word's
+// eight in one, a partial word's (ngroups of 8 in use, the rest masked) in blocks of four,
+// two or one, so that a partial word costs about its share of a full one (the block of
+// groups 0..3 drops the word of group 3 when only three are in use).  The reject bits are pushed
+// highest group first; the masked groups at the top leave zeros, excluded by vmask.
 // pair_tab holds, for each pair of lanes (2p, 2p+1) and each 4-bit code
 // (u0_2p, u0_2p+1, u1_2p, u1_2p+1), the two lanes' thresholds for their counts u
 // (m = d - u), 8 bytes per entry: one 64-bit load serves two lanes, and the code is
 // cut from the count planes with two shifts and one three-input logic op.
-template <int D>
+// FULL: the caller guarantees full words (every chain a multiple of 32 replicas), so the
+// partial-word code is left out and cannot take registers from the full-word path.
+template <int D, bool FULL = false>
 __device__ __forceinline__ uint32_t decide_site(const SiteCount<D> &cnt, const PhiloxSweep &P,
                                                 const PhiloxSite &Q, uint32_t c3base, int ngroups,
                                                 const uint2 *__restrict__ pair_tab, const Job &jb) {
   uint32_t rej = 0;
-  if (ngroups == 8) { // a full word: all eight groups in one interleaved evaluation
+  if (FULL || ngroups == 8) { // a full word: all eight groups in one interleaved evaluation
     uint4 rr[8];
     philox_finishK<8>(P, Q, c3base, 0, jb, rr);
 #pragma unroll
     for (int u = 7; u >= 0; --u) rej = decide_group<D>(rej, rr[u], u, cnt, pair_tab);
     return cnt.aut | ~rej;
   }
-#pragma unroll
-  for (int gp = 3; gp >= 0; --gp) {
-    const int ga = 2 * gp + 1, gb = 2 * gp;
-    if (ga < ngroups) {
-      uint4 rr[2];
-      philox_finishK<2>(P, Q, c3base, gb, jb, rr);
-      rej = decide_group<D>(rej, rr[1], ga, cnt, pair_tab);
-      rej = decide_group<D>(rej, rr[0], gb, cnt, pair_tab);
-    } else if (gb < ngroups) {
-      rej <<= 4;
-      const uint4 rb = philox_finish(P, Q, c3base | ((uint32_t)gb << 8), jb);
-      rej = decide_group<D>(rej, rb, gb, cnt, pair_tab);
-    } else {
-      rej <<= 8;
+  if (ngroups > 4) { // groups 4 .. ngroups - 1 first (the higher ones)
+    if (ngroups == 7) {
+      uint4 rc[1];
+      philox_finishK<1>(P, Q, c3base, 6, jb, rc);
+      rej = decide_group<D>(rej, rc[0], 6, cnt, pair_tab);
     }
+    if (ngroups >= 6) {
+      uint4 rb[2];
+      philox_finishK<2>(P, Q, c3base, 4, jb, rb);
+      rej = decide_group<D>(rej, rb[1], 5, cnt, pair_tab);
+      rej = decide_group<D>(rej, rb[0], 4, cnt, pair_tab);
+    } else {
+      uint4 rb[1];
+      philox_finishK<1>(P, Q, c3base, 4, jb, rb);
+      rej = decide_group<D>(rej, rb[0], 4, cnt, pair_tab);
+    }
+  }
+  if (ngroups >= 3) { // groups 0..3 (group 3 dropped when only three are in use)
+    uint4 ra[4];
+    philox_finishK<4>(P, Q, c3base, 0, jb, ra);
+    if (ngroups >= 4) rej = decide_group<D>(rej, ra[3], 3, cnt, pair_tab);
+    rej = decide_group<D>(rej, ra[2], 2, cnt, pair_tab);
+    rej = decide_group<D>(rej, ra[1], 1, cnt, pair_tab);
+    rej = decide_group<D>(rej, ra[0], 0, cnt, pair_tab);
+  } else if (ngroups == 2) {
+    uint4 ra[2];
+    philox_finishK<2>(P, Q, c3base, 0, jb, ra);
+    rej = decide_group<D>(rej, ra[1], 1, cnt, pair_tab);
+    rej = decide_group<D>(rej, ra[0], 0, cnt, pair_tab);
+  } else {
+    uint4 ra[1];
+    philox_finishK<1>(P, Q, c3base, 0, jb, ra);
+    rej = decide_group<D>(rej, ra[0], 0, cnt, pair_tab);
   }
   return cnt.aut | ~rej;
 }
