@@ -46,7 +46,7 @@ __device__ __forceinline__ void expand_couplings(const Geo &g, const uint32_t *j
 // (all of one sample).  Site geometry, couplings and the site-level Philox parts are
 // shared by the WPC words.  `accum` adds each site's post-update count to V[w] (a
 // run-time flag, so that both colours run one copy of the code); NOFLIP counts only.
-template <int D, int NT, int WPC, bool NOFLIP, bool FULL>
+template <int D, int NT, int WPC, bool NOFLIP, bool FULLW>
 __device__ __forceinline__ void half_sweep(const Geo &g, int col, bool accum, uint32_t *__restrict__ sp,
                                            const uint8_t *__restrict__ jbyte,
                                            const uint2 *__restrict__ pair_tab, const uint32_t *vmask,
@@ -94,7 +94,7 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, bool accum, ui
       const SiteCount<D> cnt = count_site<D>(s0, nb, jm);
       uint32_t F = 0;
       if (!NOFLIP) {
-        F = decide_site<D, FULL>(cnt, P, Q, c3base[w], ngroups[w], pair_tab + w * 256, jb) & vmask[w];
+        F = decide_site<D, FULLW>(cnt, P, Q, c3base[w], ngroups[w], pair_tab + w * 256, jb) & vmask[w];
         own[q] = s0 ^ F;
       }
       if (accum) {
@@ -236,9 +236,9 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
 // n_mcs MCS.  When the job's `fuse` flag is set the item holds whole chains (a chain is
 // Wc <= WPC words) and their exchange passes run between the MCS.  The job comes from a
 // table in parameter space, so one launch can sweep many jobs of one lattice shape.
-// FULL: every word of every job of the launch is full (each chain a multiple of 32
+// FULLW: every word of every job of the launch is full (each chain a multiple of 32
 // replicas), so the partial-word decision code is left out of the instantiation.
-template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false, bool FULL = false>
+template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false, bool FULLW = false>
 __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     k_resident_packed(const __grid_constant__ ResidentParams<MAXJ> rp) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         // the half-sweep's code
 #pragma unroll 1
         for (int col = 0; col < 2; ++col) {
-          half_sweep<D, NT, WPC, false, FULL>(g, col, col == 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
+          half_sweep<D, NT, WPC, false, FULLW>(g, col, col == 1, sp, jbyte, pair_tab, vmask, ngroups, c3base, P, jb, V);
           if (col == 0) __syncthreads();
         }
       } else {
@@ -795,27 +795,27 @@ int8_fn pick_int8(int d, int nt) {
 template <int MAXJ>
 using packed_fn = void (*)(ResidentParams<MAXJ>);
 
-template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false, bool FULL = false>
+template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false, bool FULLW = false>
 packed_fn<MAXJ> pick_packed_nt(int nt) {
   switch (nt) {
-  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS, FULL>;
-  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS, FULL>;
-  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS, FULL>;
-  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS, FULL>;
-  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS, FULL>;
+  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS, FULLW>;
+  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS, FULLW>;
+  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS, FULLW>;
+  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS, FULLW>;
+  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS, FULLW>;
   }
 }
 // the sweep kernel that measures after its last MCS (two one-word chains per CTA)
-template <bool FULL>
+template <bool FULLW>
 packed_fn<1> pick_packed_meas(int d, int nt) {
-  return d == 2 ? pick_packed_nt<2, 2, false, 1, true, FULL>(nt) : pick_packed_nt<3, 2, false, 1, true, FULL>(nt);
+  return d == 2 ? pick_packed_nt<2, 2, false, 1, true, FULLW>(nt) : pick_packed_nt<3, 2, false, 1, true, FULLW>(nt);
 }
 
-template <bool EONLY, int MAXJ, bool FULL = false>
+template <bool EONLY, int MAXJ, bool FULLW = false>
 packed_fn<MAXJ> pick_packed(int d, int nt, int wpc) {
   if (d == 2)
-    return wpc == 2 ? pick_packed_nt<2, 2, EONLY, MAXJ, false, FULL>(nt) : pick_packed_nt<2, 1, EONLY, MAXJ, false, FULL>(nt);
-  return wpc == 2 ? pick_packed_nt<3, 2, EONLY, MAXJ, false, FULL>(nt) : pick_packed_nt<3, 1, EONLY, MAXJ, false, FULL>(nt);
+    return wpc == 2 ? pick_packed_nt<2, 2, EONLY, MAXJ, false, FULLW>(nt) : pick_packed_nt<2, 1, EONLY, MAXJ, false, FULLW>(nt);
+  return wpc == 2 ? pick_packed_nt<3, 2, EONLY, MAXJ, false, FULLW>(nt) : pick_packed_nt<3, 1, EONLY, MAXJ, false, FULLW>(nt);
 }
 } // namespace
 

@@ -263,14 +263,14 @@ __device__ __forceinline__ uint32_t decide_group(uint32_t rej, const uint4 &r, i
 // (u0_2p, u0_2p+1, u1_2p, u1_2p+1), the two lanes' thresholds for their counts u
 // (m = d - u), 8 bytes per entry: one 64-bit load serves two lanes, and the code is
 // cut from the count planes with two shifts and one three-input logic op.
-// FULL: the caller guarantees full words (every chain a multiple of 32 replicas), so the
+// FULLW: the caller guarantees full words (every chain a multiple of 32 replicas), so the
 // partial-word code is left out and cannot take registers from the full-word path.
-template <int D, bool FULL = false>
+template <int D, bool FULLW = false>
 __device__ __forceinline__ uint32_t decide_site(const SiteCount<D> &cnt, const PhiloxSweep &P,
                                                 const PhiloxSite &Q, uint32_t c3base, int ngroups,
                                                 const uint2 *__restrict__ pair_tab, const Job &jb) {
   uint32_t rej = 0;
-  if (FULL || ngroups == 8) { // a full word: all eight groups in one interleaved evaluation
+  if (FULLW || ngroups == 8) { // a full word: all eight groups in one interleaved evaluation
     uint4 rr[8];
     philox_finishK<8>(P, Q, c3base, 0, jb, rr);
 #pragma unroll
