@@ -53,12 +53,17 @@ __device__ __forceinline__ void half_sweep(const Geo &g, int col, bool accum, ui
                                            const int *ngroups, const uint32_t *c3base, const PhiloxSweep &P,
                                            const Job &jb, uint32_t (&V)[WPC][NB], int wcount = WPC) {
   const int H = g.H, L1 = g.L1, Nh = g.Nh, N = g.N;
+  // q / H and row / L1 as a multiply-high by ceil(2^32 / divisor) (division by an
+  // invariant integer, Granlund and Montgomery 1994): exact while the dividend times the
+  // divisor stays below 2^32, which holds for every lattice that fits in shared memory
+  const uint32_t mH = H > 1 ? 0xFFFFFFFFu / (uint32_t)H + 1u : 0u;
+  const uint32_t mL1 = L1 > 1 ? 0xFFFFFFFFu / (uint32_t)L1 + 1u : 0u;
   for (int q = threadIdx.x; q < Nh; q += NT) {
-    const int row = q / H;
+    const int row = H > 1 ? (int)__umulhi((uint32_t)q, mH) : q;
     const int k = q - row * H;
     int y, z;
     if (D == 3) {
-      z = row / L1;
+      z = L1 > 1 ? (int)__umulhi((uint32_t)row, mL1) : row;
       y = row - z * L1;
     } else {
       y = row;
