@@ -31,16 +31,6 @@ namespace {
 
 constexpr int HNT = 1024; // threads per CTA (32 warps)
 
-// Canonical site of bitmap block b, lane l (row r = b / RW, x = 32 (b % RW) + l) as a
-// colour-split index p; `valid` is false for the padding bits past L0.
-__device__ __forceinline__ int block_site(const Geo &g, int RW, int b, int l, bool &valid) {
-  const int r = b / RW, x = 32 * (b - r * RW) + l;
-  valid = x < g.L0;
-  const int y = r % g.L1, z = r / g.L1;
-  const int c = (x + y + z) & 1;
-  return c * g.Nh + r * g.H + (x >> 1);
-}
-
 // Phase 0: the two chains' slot maps of sample s and the byte tables of the lane
 // permutations: sig maps chain-1 lane b -> chain-0 lane a = perm0[slot1[b]] (built when
 // `sig` is given), sigi maps chain-0 lane a -> chain-1 lane b = perm1[slot0[a]] (when
@@ -71,13 +61,6 @@ __device__ __forceinline__ void houd_tables(const Job &jb, const Dev &dv, int s,
     if (sigi) sigi[e] = o2;
   }
   __syncthreads();
-}
-
-// The chain-0 lanes whose pair takes part in the move: a < T at a slot below hK.  A pair
-// outside it gets an empty q bitmap, hence M = 0 and no move.  Needs slot0 (phase 0).
-__device__ __forceinline__ uint32_t houd_pair_mask(const Job &jb, const int32_t *slot0) {
-  const int lane = threadIdx.x & 31;
-  return __ballot_sync(FULLM, lane < jb.T && slot0[lane] < jb.hK);
 }
 
 // Phase 1: the q bitmap of every pair of sample s (pair a's bitmap at Qb + a * NBW) and
@@ -928,17 +911,28 @@ bool houdayer_labels(const Job &jb) {
 
 // With `scratch` (houdayer_scratch_bytes of the handle's buffer) the split form runs;
 // without it the single-CTA form, whose bitmaps must then fit `smem_limit`.
+HoudMaps houd_maps_of(const Job &jb, uint32_t *scratch) {
+  HoudMaps hm;
+  hm.RW = (jb.g.L0 + 31) / 32;
+  hm.NBW = jb.g.R * hm.RW;
+  hm.Qg = scratch;
+  hm.Cg = scratch + (size_t)jb.S * jb.T * hm.NBW;
+  hm.Mg = hm.Cg + (size_t)jb.S * jb.T * hm.NBW;
+  return hm;
+}
+
 cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, bool multi,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool fused) {
   const int RW = (jb.g.L0 + 31) / 32;
   const int NBW = jb.g.R * RW;
   if (scratch) {
+    const HoudMaps hm = houd_maps_of(jb, scratch);
     HoudSplit hs;
-    hs.RW = RW;
-    hs.NBW = NBW;
-    hs.Qg = scratch;
-    hs.Cg = scratch + (size_t)jb.S * jb.T * NBW;
-    hs.Mg = hs.Cg + (size_t)jb.S * jb.T * NBW;
+    hs.RW = hm.RW;
+    hs.NBW = hm.NBW;
+    hs.Qg = hm.Qg;
+    hs.Cg = hm.Cg;
+    hs.Mg = hm.Mg;
     hs.queue = hs.Mg + (size_t)jb.S * 32;
     int smem = 0;
     fill_shape(jb, NBW, &hs.wpb, &hs.in_smem, &smem);
@@ -951,9 +945,15 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
     parts = parts < 1 ? 1 : (parts > 8 ? 8 : parts);
     parts = parts > tiles ? tiles : parts;
     const dim3 pgrid((unsigned)jb.S, (unsigned)parts);
-    cudaError_t e0 = cudaMemsetAsync(hs.Mg, 0, (size_t)jb.S * 32 * 4 + 16, st); // M and the pair queue
-    if (e0 != cudaSuccess) return e0;
-    k_houd_q<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    if (fused) {
+      // M was written whole by the sweep launch: only the pair queue is cleared
+      const cudaError_t e0 = cudaMemsetAsync(hs.queue, 0, 16, st);
+      if (e0 != cudaSuccess) return e0;
+    } else {
+      const cudaError_t e0 = cudaMemsetAsync(hs.Mg, 0, (size_t)jb.S * 32 * 4 + 16, st); // M and the pair queue
+      if (e0 != cudaSuccess) return e0;
+      k_houd_q<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    }
     const int lab = label_smem_bytes(NBW, jb.g.N, jb.g.R, jb.g.d);
     // the single-cluster move grows only the seed's cluster where a fill form applies
     bool seeded = false;
@@ -970,9 +970,10 @@ cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int
       pick_fill(jb.g.d, RW, hs.in_smem != 0)<<<(unsigned)((pairs + hs.wpb - 1) / hs.wpb), 32 * hs.wpb,
                                                 (size_t)smem, st>>>(jb, dv, hs);
     }
-    k_houd_flip<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
+    if (!fused) k_houd_flip<<<pgrid, HSPLIT_NT, 0, st>>>(jb, dv, hs);
     return cudaGetLastError();
   }
+  if (fused) return cudaErrorInvalidValue; // the fused phases need the split form's scratch
   if (multi) return cudaErrorNotSupported; // the multi-cluster variant labels in the split form only
   HoudArgs ha;
   ha.RW = RW;

@@ -16,6 +16,7 @@
 // their (post-update) unsatisfied count; E = 2U - dN.  The sums are kept as bit-sliced
 // vertical counters per thread and reduced across the CTA once per sweep, so E is
 // recomputed exactly every sweep instead of being accumulated from flips.
+#include "sgmc_houd.cuh"
 #include "sgmc_internal.cuh"
 #include "sgmc_sweep.cuh"
 #include "sgmc_tma.cuh"
@@ -243,7 +244,10 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
 // table in parameter space, so one launch can sweep many jobs of one lattice shape.
 // FULLW: every word of every job of the launch is full (each chain a multiple of 32
 // replicas), so the partial-word decision code is left out of the instantiation.
-template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false, bool FULLW = false>
+// HOUD (single-job launches whose CTAs hold both one-word chains of a sample): 1, after
+// the last sweep write the Houdayer move's q bitmaps and M of every pair; 2 (energy
+// only, right after the move's cluster phase), first apply the move's cluster flips.
+template <int D, int NT, int WPC, bool ENERGY_ONLY, int MAXJ, bool MEAS = false, bool FULLW = false, int HOUD = 0>
 __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     k_resident_packed(const __grid_constant__ ResidentParams<MAXJ> rp) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -351,8 +355,58 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       atomicOr(&dv.ctr[CTR_ERROR], ERR_TMA_TIMEOUT);
       mbar_wait(bar, 0, MBAR_MAX_TRIES); // let copies still in flight land before exiting
     }
-    job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, 0ull);
+    job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD == 2 ? 1ull : 0ull);
     return;
+  }
+  if constexpr (HOUD == 2) {
+    // Houdayer move, phase 3 (Eq. 10): on pair a's cluster (chain-0 lane a with the
+    // chain-1 lane b = perm1[slot0[a]] of the same slot) both replicas flip.  A warp
+    // transposes the pairs' cluster bitmap words of a 32-site block (lane l: bit a = site l
+    // in pair a's cluster); the chain-0 word takes the mask as is, the chain-1 word its
+    // permutation a -> b.  Pairs without a q = -1 site (M = 0) have no bitmap.
+    uint32_t *sigi = reinterpret_cast<uint32_t *>(pair_tab); // 1024 words: byte tables a -> b
+    const int T = jb.T, NBW = rp.hm.NBW, RW = rp.hm.RW;
+    for (int e = tid; e < 1024; e += NT) {
+      const int j = e >> 8, v = e & 255;
+      uint32_t o = 0u;
+#pragma unroll
+      for (int bb = 0; bb < 8; ++bb) {
+        const int a = 8 * j + bb;
+        if (((v >> bb) & 1) && a < T) o |= 1u << PM(1)[SL(0)[a]];
+      }
+      sigi[e] = o;
+    }
+    const uint32_t skip = __ballot_sync(FULL, lane >= T || rp.hm.Mg[(size_t)s * 32 + lane] == 0u);
+    const bool mine = lane < T && !((skip >> lane) & 1u);
+    const uint32_t *Cb = rp.hm.Cg + (size_t)s * T * NBW + (size_t)lane * NBW;
+    __syncthreads();
+    // a warp takes 4 consecutive blocks at a time: lane a loads them as one 16-byte word
+    // of pair a's bitmap (bitmaps of a multiple of 4 words; one block at a time otherwise)
+    const int G = NBW % 4 == 0 ? 4 : 1;
+    for (int b0 = warp * G; b0 < NBW; b0 += (NT / 32) * G) {
+      uint32_t cw[4] = {0u, 0u, 0u, 0u};
+      if (mine) {
+        if (G == 4) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(Cb + b0);
+          cw[0] = v.x, cw[1] = v.y, cw[2] = v.z, cw[3] = v.w;
+        } else {
+          cw[0] = Cb[b0];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < G && __any_sync(FULL, cw[u] != 0u)) {
+          const uint32_t f = transpose32(cw[u], lane);
+          bool valid;
+          const int p = block_site(g, RW, b0 + u, lane, valid);
+          if (valid && f) {
+            sp[p] ^= f;
+            sp[g.N + p] ^= permute_word(sigi, f);
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
   if (!ENERGY_ONLY && warp < WPC) {
     const int kslot = lane < my_nvalid ? (fuse ? SL(my_ci)[my_j0 + lane] : dv.slot[my_cb + my_j0 + lane]) : 0;
@@ -510,6 +564,63 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       if (tid < T) rp.mQ[(size_t)s * T + SL(0)[tid]] = g.N - 2 * (int32_t)tot[tid];
     }
   }
+  if constexpr (HOUD == 1) {
+    // Houdayer move, phase 1 (Eq. 10) on the final configurations: per site the chain-1
+    // word is permuted lane b -> lane a = perm0[slot1[b]] (byte tables), so that bit a of
+    // w0 ^ sigma(w1) is q = -1 of pair a; a warp transposes 32 sites x 32 pairs, giving
+    // each pair's bitmap word of the block, and M counts the q = -1 sites of each pair.
+    // Only pairs at a slot below hK take part (the others get an empty bitmap).
+    __syncthreads(); // every warp is past its last half-sweep: the pair tables are free
+    int32_t *maps = ptw; // perm0, perm1, slot0, slot1 [32 each], then M [32]
+    uint32_t *Mc = reinterpret_cast<uint32_t *>(ptw + 128);
+    const int T = jb.T, NBW = rp.hm.NBW, RW = rp.hm.RW;
+    if (warp < 2) {
+      const size_t cb = ((size_t)s * 2 + warp) * T;
+      maps[warp * 32 + lane] = lane < T ? dv.perm[cb + lane] : 0;
+      maps[64 + warp * 32 + lane] = lane < T ? dv.slot[cb + lane] : 0;
+    }
+    if (tid < 32) Mc[tid] = 0u;
+    __syncthreads();
+    uint32_t *sig = reinterpret_cast<uint32_t *>(pair_tab); // 1024 words
+    for (int e = tid; e < 1024; e += NT) {
+      const int j = e >> 8, v = e & 255;
+      uint32_t o = 0u;
+#pragma unroll
+      for (int bb = 0; bb < 8; ++bb) {
+        const int b = 8 * j + bb;
+        if (((v >> bb) & 1) && b < T) o |= 1u << maps[maps[96 + b]];
+      }
+      sig[e] = o;
+    }
+    const uint32_t tmask = houd_pair_mask(jb, maps + 64);
+    uint32_t *Qb = rp.hm.Qg + (size_t)s * T * NBW + (size_t)lane * NBW;
+    uint32_t mpart = 0u;
+    __syncthreads();
+    // a warp takes 4 consecutive blocks at a time: lane a stores them as one 16-byte word
+    // of pair a's bitmap (bitmaps of a multiple of 4 words; one block at a time otherwise)
+    const int G = NBW % 4 == 0 ? 4 : 1;
+    for (int b0 = warp * G; b0 < NBW; b0 += (NT / 32) * G) {
+      uint32_t col[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        col[u] = 0u;
+        if (u < G) {
+          bool valid;
+          const int p = block_site(g, RW, b0 + u, lane, valid);
+          const uint32_t qa = valid ? (sp[p] ^ permute_word(sig, sp[g.N + p])) & tmask : 0u;
+          col[u] = transpose32(qa, lane); // lane a: bit l = q of pair a at site l
+        }
+      }
+      if (lane < T) {
+        if (G == 4) *reinterpret_cast<uint4 *>(Qb + b0) = make_uint4(col[0], col[1], col[2], col[3]);
+        else Qb[b0] = col[0];
+        mpart += __popc(col[0]) + __popc(col[1]) + __popc(col[2]) + __popc(col[3]);
+      }
+    }
+    if (lane < T && mpart) atomicAdd(&Mc[lane], mpart);
+    __syncthreads();
+    if (tid < 32) rp.hm.Mg[(size_t)s * 32 + tid] = Mc[tid]; // the CTA holds the whole sample
+  }
   if (nch > 0 && warp < WPC && lane < my_nvalid) dv.E[my_cb + my_j0 + lane] = EL(my_ci)[my_j0 + lane];
   if (warp < nch) {
     const size_t cb = ((size_t)s * jb.C + c0 + warp) * jb.T;
@@ -534,12 +645,12 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       dv.trip_sum[chain] += *TSUM(warp);
     }
   }
-  if (!ENERGY_ONLY) {
+  if (!ENERGY_ONLY || HOUD == 2) {
     fence_proxy_async(); // this thread's shared-memory writes -> visible to the TMA store
     __syncthreads();
     if (tid == 0) bulk_s2g_and_wait(gsp, sp, 4u * (uint32_t)(g.N * WPC));
   }
-  job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, 0ull);
+  job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD == 2 ? 1ull : 0ull);
 }
 
 // A colour-`col` site of the int8 kernel, from its offset q in the colour's half: its
@@ -800,15 +911,23 @@ int8_fn pick_int8(int d, int nt) {
 template <int MAXJ>
 using packed_fn = void (*)(ResidentParams<MAXJ>);
 
-template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false, bool FULLW = false>
+template <int D, int WPC, bool EONLY, int MAXJ, bool MEAS = false, bool FULLW = false, int HOUD = 0>
 packed_fn<MAXJ> pick_packed_nt(int nt) {
   switch (nt) {
-  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS, FULLW>;
-  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS, FULLW>;
-  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS, FULLW>;
-  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS, FULLW>;
-  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS, FULLW>;
+  case 64: return k_resident_packed<D, 64, WPC, EONLY, MAXJ, MEAS, FULLW, HOUD>;
+  case 128: return k_resident_packed<D, 128, WPC, EONLY, MAXJ, MEAS, FULLW, HOUD>;
+  case 256: return k_resident_packed<D, 256, WPC, EONLY, MAXJ, MEAS, FULLW, HOUD>;
+  case 512: return k_resident_packed<D, 512, WPC, EONLY, MAXJ, MEAS, FULLW, HOUD>;
+  default: return k_resident_packed<D, 1024, WPC, EONLY, MAXJ, MEAS, FULLW, HOUD>;
   }
+}
+// the kernels that take a phase of the Houdayer move (two one-word chains per CTA):
+// HOUD 1 the sweeps before it (q bitmaps out), HOUD 2 the energies after it (flips in)
+template <int HOUD, bool FULLW = false>
+packed_fn<1> pick_packed_houd(int d, int nt) {
+  constexpr bool EONLY = HOUD == 2;
+  return d == 2 ? pick_packed_nt<2, 2, EONLY, 1, false, FULLW, HOUD>(nt)
+                : pick_packed_nt<3, 2, EONLY, 1, false, FULLW, HOUD>(nt);
 }
 // the sweep kernel that measures after its last MCS (two one-word chains per CTA)
 template <bool FULLW>
@@ -826,7 +945,7 @@ packed_fn<MAXJ> pick_packed(int d, int nt, int wpc) {
 
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
-                            int32_t *meas_E, int32_t *meas_Q, bool after_move) {
+                            int32_t *meas_E, int32_t *meas_Q, bool after_move, const HoudMaps *hm, int houd) {
   if (int8fmt) {
     // small chains: enough threads that a half-sweep is one pass of (group, 32 sites) items
     const int chunks = (jb.Tp / 4) * ((jb.g.Nh + 31) / 32);
@@ -856,7 +975,19 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
   rp.jobs[0].fuse = fuse_pt ? 1 : 0;
   rp.jobs[0].n_metro = n_metro;
   const bool full = jb.T % 32 == 0; // every word of the job is full
-  const packed_fn<1> fn = meas ? (full ? pick_packed_meas<true>(jb.g.d, nthreads) : pick_packed_meas<false>(jb.g.d, nthreads))
+  if (houd != 0) {
+    // a phase of the Houdayer move: the CTA must hold both one-word chains of its sample
+    const bool ok = hm && !int8fmt && wpc == 2 && jb.C == 2 && jb.Wc == 1 && !meas &&
+                    (houd == 1 ? !energy_only : (houd == 2 && energy_only && after_move && fuse_pt));
+    if (!ok) return cudaErrorInvalidValue;
+    rp.hm = *hm;
+  } else {
+    rp.hm = HoudMaps{};
+  }
+  const packed_fn<1> fn = houd == 1    ? (full ? pick_packed_houd<1, true>(jb.g.d, nthreads)
+                                               : pick_packed_houd<1, false>(jb.g.d, nthreads))
+                          : houd == 2  ? pick_packed_houd<2>(jb.g.d, nthreads)
+                          : meas       ? (full ? pick_packed_meas<true>(jb.g.d, nthreads) : pick_packed_meas<false>(jb.g.d, nthreads))
                           : energy_only ? pick_packed<true, 1>(jb.g.d, nthreads, wpc)
                           : full        ? pick_packed<false, 1, true>(jb.g.d, nthreads, wpc)
                                         : pick_packed<false, 1>(jb.g.d, nthreads, wpc);
@@ -903,6 +1034,9 @@ cudaError_t prepare_resident_kernels(int max_smem) {
         if (wpc == 2) {
           fns.push_back((const void *)pick_packed_meas<false>(d, nt));
           fns.push_back((const void *)pick_packed_meas<true>(d, nt));
+          fns.push_back((const void *)pick_packed_houd<1, false>(d, nt));
+          fns.push_back((const void *)pick_packed_houd<1, true>(d, nt));
+          fns.push_back((const void *)pick_packed_houd<2>(d, nt));
         }
       }
   for (int d = 2; d <= 3; ++d)

@@ -305,9 +305,9 @@ sg_status recompute_energy(sg_handle *h, cudaStream_t st) {
 }
 
 // The cluster move itself (spins only; energies are stale until recomputed).
-sg_status houdayer_move(sg_handle *h, cudaStream_t st, bool multi) {
+sg_status houdayer_move(sg_handle *h, cudaStream_t st, bool multi, bool fused = false) {
   uint32_t *scratch = h->lay.houd_bytes ? reinterpret_cast<uint32_t *>(h->buf + h->lay.houd) : nullptr;
-  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, HOUD_SMEM_BUDGET, multi, st));
+  sg_status r = check(h, launch_houdayer(h->job, h->dev, scratch, HOUD_SMEM_BUDGET, multi, st, fused));
   if (r == SG_OK) h->t_houd += 1;
   return r;
 }
@@ -534,6 +534,14 @@ bool multi_possible(const sg_handle *h) {
   return houdayer_possible(&h->p, h->job) && h->lay.houd_bytes > 0 && houdayer_labels(h->job);
 }
 
+// Whether an MCS with the move can give its first and last phases to the resident
+// launches around it: packed spins in shared memory, one CTA per sample holding both
+// one-word chains, the bitmap scratch present, the exchange fused.
+bool houd_fused(const sg_handle *h) {
+  return h->p.houdayer && h->fuse_pt && !h->global && !h->int8fmt && !h->gauss && h->lay.houd_bytes > 0 &&
+         h->wpc == 2 && h->job.C == 2 && h->job.Wc == 1 && houdayer_possible(&h->p, h->job);
+}
+
 sg_status sg_houdayer_multi(sg_handle *h, uintptr_t stream) {
   if (h && h->gauss) return SG_EUNSUPPORTED; // +-J (or packed-spin) only
   if (!h) return SG_EINVAL;
@@ -561,6 +569,24 @@ sg_status mcs_ops(sg_handle *h, int n_mcs, cudaStream_t st) {
   }
   if (h->p.houdayer && !houdayer_possible(&h->p, h->job)) return SG_EUNSUPPORTED;
   if (h->p.houdayer == 2 && !multi_possible(h)) return SG_EUNSUPPORTED;
+  if (houd_fused(h)) {
+    // the move's q bitmaps come out of the sweep launch and its flips go into the energy
+    // launch, which also runs the exchange: three launches per MCS around the cluster phase
+    const sgmc::HoudMaps hm = sgmc::houd_maps_of(h->job, reinterpret_cast<uint32_t *>(h->buf + h->lay.houd));
+    for (int m = 0; m < n_mcs; ++m) {
+      sg_status r = check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, false, false, h->smem, st,
+                                                   nm, 1, nullptr, nullptr, false, &hm, 1));
+      if (r != SG_OK) return r;
+      h->t_metro += (uint64_t)nm;
+      r = houdayer_move(h, st, h->p.houdayer == 2, true);
+      if (r != SG_OK) return r;
+      r = check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, true, true, h->smem, st, 1, 1, nullptr,
+                                         nullptr, true, &hm, 2));
+      if (r != SG_OK) return r;
+      h->t_pt += 1;
+    }
+    return SG_OK;
+  }
   for (int m = 0; m < n_mcs; ++m) {
     sg_status r = sweeps(h, nm, st);
     if (r == SG_OK && h->p.houdayer) {

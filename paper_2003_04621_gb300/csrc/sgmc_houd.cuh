@@ -94,6 +94,23 @@ __device__ __forceinline__ void close_row(const uint32_t (&Q)[RW], const uint32_
   }
 }
 
+// Canonical site of bitmap block b, lane l (row r = b / RW, x = 32 (b % RW) + l) as a
+// colour-split index p; `valid` is false for the padding bits past L0.
+__device__ __forceinline__ int block_site(const Geo &g, int RW, int b, int l, bool &valid) {
+  const int r = b / RW, x = 32 * (b - r * RW) + l;
+  valid = x < g.L0;
+  const int y = r % g.L1, z = r / g.L1;
+  const int c = (x + y + z) & 1;
+  return c * g.Nh + r * g.H + (x >> 1);
+}
+
+// The chain-0 lanes whose pair takes part in the move: a < T at a slot below hK.  A pair
+// outside it gets an empty q bitmap, hence M = 0 and no move.  Needs slot0 (phase 0).
+__device__ __forceinline__ uint32_t houd_pair_mask(const Job &jb, const int32_t *slot0) {
+  const int lane = threadIdx.x & 31;
+  return __ballot_sync(FULLM, lane < jb.T && slot0[lane] < jb.hK);
+}
+
 struct HoudSplit {
   int RW;        // words per bitmap row
   int NBW;       // words per bitmap

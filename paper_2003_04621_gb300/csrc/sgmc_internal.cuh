@@ -137,6 +137,17 @@ struct JobDesc {
 
 // Kernel parameters of the resident kernel: up to MAXJ jobs of one lattice shape.  The
 // table lives in the kernel's parameter space (read through constant memory).
+// The Houdayer move's bitmap scratch of one job, for the sweep kernels that take the
+// move's first and last phases (the q bitmaps after the sweeps, the cluster flips before
+// the energies): [S][T][NBW] q and cluster bitmaps and [S][32] M per pair.
+struct HoudMaps {
+  uint32_t *Qg;
+  uint32_t *Cg;
+  uint32_t *Mg;
+  int RW;  // words per bitmap row
+  int NBW; // words per bitmap
+};
+
 template <int MAXJ>
 struct ResidentParams {
   int n_jobs;
@@ -146,6 +157,7 @@ struct ResidentParams {
   // single-job launches of two one-word chains per CTA: after the last MCS, E by slot
   // [S][2][T] and N q [S][T] into these device arrays (null: no measurement)
   int32_t *mE, *mQ;
+  HoudMaps hm; // single-job launches that take a phase of the Houdayer move
   JobDesc jobs[MAXJ];
 };
 constexpr int MAX_BATCH_JOBS = 96;
@@ -417,9 +429,13 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 }
 
 // Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
+// houd = 1: after the last sweep, the Houdayer q bitmaps and M of every pair into *hm;
+// houd = 2 (energy-only after a move): first the cluster flips from *hm.  Both need a CTA
+// that holds both one-word chains of a sample (wpc 2, two chains of T <= 32).
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
-                            int32_t *meas_E = nullptr, int32_t *meas_Q = nullptr, bool after_move = false);
+                            int32_t *meas_E = nullptr, int32_t *meas_Q = nullptr, bool after_move = false,
+                            const HoudMaps *hm = nullptr, int houd = 0);
 // Several jobs of the same lattice shape in one launch (chunks of MAX_BATCH_JOBS).
 // jobs[i].n_items/fuse/n_metro must be filled; first_item is set here.
 cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int wpc, size_t smem, cudaStream_t st,
@@ -440,8 +456,12 @@ int houdayer_smem(const Job &jb, int bitmaps_smem);
 size_t houdayer_scratch_bytes(const Job &jb);
 // Whether the labelling kernel (and so the multi-cluster variant) runs for this lattice.
 bool houdayer_labels(const Job &jb);
+// fused: the sweep launch before wrote the q bitmaps and M, and the energy launch after
+// applies the flips (launch_resident houd = 1 / 2), so only the cluster phase runs here.
 cudaError_t launch_houdayer(const Job &jb, const Dev &dv, uint32_t *scratch, int smem_limit, bool multi,
-                            cudaStream_t st);
+                            cudaStream_t st, bool fused = false);
+// The bitmap scratch layout of the split form inside `scratch`.
+HoudMaps houd_maps_of(const Job &jb, uint32_t *scratch);
 } // namespace sgmc
 
 namespace sgmc {

@@ -84,6 +84,28 @@ def test_houdayer_mcs_2d_l128(oracle_mod):
     assert orc.counters()["houd_moves"] > 0
 
 
+@pytest.mark.parametrize("multi", [False, True])
+@pytest.mark.parametrize("ndim,dims,T", [(2, (64, 32), 24), (3, (8, 8, 8), 12), (3, (8, 6, 4), 32)])
+def test_houdayer_mcs_fused_and_split_phases(oracle_mod, multi, ndim, dims, T):
+    """The MCS with the move, once with its q bitmaps and flips taken by the resident
+    launches around the cluster phase (two one-word chains per CTA), once with the three
+    separate move kernels (one word per CTA): both equal the oracle after every MCS."""
+    kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.3, 1.8, T), sim_seed=11,
+              coupling_seed=2, houdayer=2 if multi else True)
+    states = []
+    for words in (2, 1):
+        sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+        sim.set_launch(256, words)
+        assert sim.launch()["words"] == words
+        for t in range(5):
+            sim.run_mcs(1)
+            orc.mcs(1, houdayer=kw["houdayer"])
+            assert_same_state(sim, orc, f"words {words} mcs {t}")
+        assert sim.counters()["houdayer_sites"] == orc.counters()["houd_flipped"]
+        states.append(sim.spins().cpu().numpy())
+    np.testing.assert_array_equal(states[0], states[1])
+
+
 def test_houdayer_cold_percolating_clusters(oracle_mod):
     """Low temperatures and a q field of many large clusters (chains started apart)."""
     kw = dict(ndim=2, dims=(64, 32), n_samples=2, n_chains=2, temps=geometric_temps(0.05, 0.3, 6), sim_seed=3,
