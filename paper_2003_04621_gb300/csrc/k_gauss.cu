@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(GNT) k_gauss_int8(Job jb, Dev dv, int n_mcs, i
   if (!ENERGY_ONLY) {
     fence_proxy_async();
     __syncthreads();
-    if (tid == 0) bulk_s2g_and_wait(gsp, sp8, (uint32_t)(N * Tp));
+    if (tid == 0) bulk_s2g_and_release(gsp, sp8, (uint32_t)(N * Tp));
   }
   grid_done_advance(dv.ctr, adv_metro, adv_pt, 0ull);
 }

@@ -313,13 +313,19 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   uint32_t *gsp = dv.spins + ((size_t)s * jb.W + w0) * g.N; // WPC consecutive word lattices
   const uint32_t *gj = dv.jbits + (size_t)s * D * g.NW;
 
-  if (tid == 0) mbar_init(bar, 1);
+  // two transactions: the coupling planes (bar[0]) are expanded and the threshold tables
+  // filled while the larger spin lattices (bar[1]) are still in flight
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+  }
   __syncthreads();
   if (tid == 0) {
     const uint32_t sbytes = 4u * (uint32_t)(g.N * WPC), jbytes = 4u * (uint32_t)(D * g.NW);
-    mbar_expect_tx(bar, sbytes + jbytes);
-    bulk_g2s(sp, gsp, sbytes, bar);
+    mbar_expect_tx(bar, jbytes);
     bulk_g2s(jpl, gj, jbytes, bar);
+    mbar_expect_tx(bar + 1, sbytes);
+    bulk_g2s(sp, gsp, sbytes, bar + 1);
   }
   // warp w < WPC owns local word w: its chain slot, replica offset and valid lanes
   const int my_c = (w0 + warp) / jb.Wc;
@@ -349,11 +355,20 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       *TSUM(warp) = 0ull;
     }
   }
-  const bool ok = mbar_wait(bar, 0, MBAR_MAX_TRIES);
-  if (__syncthreads_or(!ok)) {
+  __syncthreads(); // the chains' maps
+  const bool okj = mbar_wait(bar, 0, MBAR_MAX_TRIES);
+  if (!ENERGY_ONLY && warp < WPC) {
+    const int kslot = lane < my_nvalid ? (fuse ? SL(my_ci)[my_j0 + lane] : dv.slot[my_cb + my_j0 + lane]) : 0;
+    fill_pair_table<D>(pair_tab + warp * 256, lane, kslot, my_nvalid, dv.thr);
+  }
+  expand_couplings<D, NT>(g, jpl, jbyte); // (read but unused if the copy timed out)
+  const bool oks = mbar_wait(bar + 1, 0, MBAR_MAX_TRIES);
+  if (__syncthreads_or(!(okj && oks))) {
     if (tid == 0) {
       atomicOr(&dv.ctr[CTR_ERROR], ERR_TMA_TIMEOUT);
-      mbar_wait(bar, 0, MBAR_MAX_TRIES); // let copies still in flight land before exiting
+      // let copies still in flight land before exiting
+      mbar_wait(bar, 0, MBAR_MAX_TRIES);
+      mbar_wait(bar + 1, 0, MBAR_MAX_TRIES);
     }
     job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD == 2 ? 1ull : 0ull);
     return;
@@ -408,11 +423,8 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     }
     __syncthreads();
   }
-  if (!ENERGY_ONLY && warp < WPC) {
-    const int kslot = lane < my_nvalid ? (fuse ? SL(my_ci)[my_j0 + lane] : dv.slot[my_cb + my_j0 + lane]) : 0;
-    fill_pair_table<D>(pair_tab + warp * 256, lane, kslot, my_nvalid, dv.thr);
-  }
-  expand_couplings<D, NT>(g, jpl, jbyte);
+  // the sweeps start after a full barrier (which also keeps the prologue's values out of
+  // the sweep loop's register allocation)
   __syncthreads();
 
   const bool warp_owned = !ENERGY_ONLY && (nch == 0 || (jb.Wc == 1 && nch == WPC));
@@ -648,7 +660,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   if (!ENERGY_ONLY || HOUD == 2) {
     fence_proxy_async(); // this thread's shared-memory writes -> visible to the TMA store
     __syncthreads();
-    if (tid == 0) bulk_s2g_and_wait(gsp, sp, 4u * (uint32_t)(g.N * WPC));
+    if (tid == 0) bulk_s2g_and_release(gsp, sp, 4u * (uint32_t)(g.N * WPC));
   }
   job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD == 2 ? 1ull : 0ull);
 }
@@ -877,7 +889,7 @@ __global__ void __launch_bounds__(NT) k_resident_int8(Job jb, Dev dv, int n_mcs,
   if (!ENERGY_ONLY) {
     fence_proxy_async();
     __syncthreads();
-    if (tid == 0) bulk_s2g_and_wait(gsp, sp8, (uint32_t)(g.N * Tp));
+    if (tid == 0) bulk_s2g_and_release(gsp, sp8, (uint32_t)(g.N * Tp));
   }
   grid_done_advance(dv.ctr, adv_metro, adv_pt, 0ull);
 }

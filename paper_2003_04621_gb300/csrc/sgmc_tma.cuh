@@ -50,14 +50,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
   return false;
 }
 
-// Shared -> global bulk copy, then wait until it has completed.  Every thread that
-// wrote the source must have run fence_proxy_async() and a barrier before this.
-__device__ __forceinline__ void bulk_s2g_and_wait(void *dst, const void *src, uint32_t bytes) {
+// Shared -> global bulk copy at the end of a kernel, then wait until the copy has read
+// its shared-memory source (so the CTA may exit); the global writes complete with the
+// grid, before any later kernel runs.  Every thread that wrote the source must have run
+// fence_proxy_async() and a barrier before this.
+__device__ __forceinline__ void bulk_s2g_and_release(void *dst, const void *src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
                "r"(bytes)
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 constexpr uint32_t MBAR_MAX_TRIES = 1u << 22;
