@@ -260,6 +260,18 @@ sg_status sg_thresholds(sg_handle *h, uint32_t *thr_out);
  * SG_EUNSUPPORTED and the previous shape is kept.  Host-only; no device work. */
 sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words);
 
+/* Paired last words (a tuning knob, on by default).  For two chains whose last
+ * 32-replica word holds at most 16 replicas (n_temps <= 16, or 33..48), the fused MCS
+ * (sg_run_mcs without the cluster move, and batches) may hold a whole sample per CTA
+ * and sweep the two chains' last words as ONE word: lanes 0..15 chain 0's, 16..31 chain
+ * 1's.  Every replica draws the same Philox words and takes the same decisions, so the
+ * results are bit-identical either way; the per-site work of one word is saved.  The
+ * words are re-split in global memory after every launch; the unused lanes of those
+ * last words (replicas >= n_temps) are then 0.
+ *   on  1 allows pairing where it applies (shape, shared memory), 0 never pairs
+ * SG_EINVAL for another value.  Host-only; no device work. */
+sg_status sg_set_pairing(sg_handle *h, int32_t on);
+
 /* Current launch shape: threads, words per CTA (-1: streaming path), shared memory bytes. */
 sg_status sg_get_launch(sg_handle *h, int32_t *threads, int32_t *words, int32_t *smem_bytes);
 

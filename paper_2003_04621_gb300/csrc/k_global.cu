@@ -54,8 +54,8 @@ __global__ void k_pair_tables(Job jb, Dev dv, uint2 *tables) {
   const int nvalid = min(32, jb.T - wc * 32);
   const size_t cb = ((size_t)s * jb.C + c) * jb.T;
   const int kslot = lane < nvalid ? dv.slot[cb + wc * 32 + lane] : 0;
-  if (jb.g.d == 3) fill_pair_table<3>(tables + (size_t)warp_id * 256, lane, kslot, nvalid, dv.thr);
-  else fill_pair_table<2>(tables + (size_t)warp_id * 256, lane, kslot, nvalid, dv.thr);
+  if (jb.g.d == 3) fill_pair_table<3>(tables + (size_t)warp_id * 256, lane, kslot, lane < nvalid, dv.thr);
+  else fill_pair_table<2>(tables + (size_t)warp_id * 256, lane, kslot, lane < nvalid, dv.thr);
 }
 
 template <int D, bool ACCUM, bool NOFLIP>

@@ -43,6 +43,7 @@ struct sg_handle {
   int wpc;         // 32-replica words per CTA of the packed resident kernel
   size_t smem;     // its dynamic shared memory
   bool fuse_pt;    // the exchange can run inside the resident kernel
+  bool pair_on;    // fused MCS may pair the chains' partial last words (sg_set_pairing)
   bool global;     // sweeps stream the lattice from global memory (no resident kernel)
   bool gauss;      // general fixed-point couplings (k_gauss.cu)
   int n_ctr;       // counters in the device array
@@ -269,7 +270,8 @@ template <bool FUSE, bool EONLY>
 sg_status launch_resident(sg_handle *h, cudaStream_t st, int n_mcs, int n_metro) {
   if (h->gauss) return check(h, sgmc::launch_gauss(h->job, h->dev, FUSE, EONLY, st, n_mcs, n_metro));
   return check(h, sgmc::launch_resident(h->job, h->dev, h->int8fmt != 0, h->nt, h->wpc, FUSE, EONLY, h->smem, st,
-                                        n_mcs, n_metro));
+                                        n_mcs, n_metro, nullptr, nullptr, false, nullptr, 0,
+                                        FUSE && !EONLY && h->pair_on));
 }
 
 cudaStream_t as_stream(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -433,6 +435,7 @@ sg_status sg_create(const sg_params *p, void *device_buf, size_t bytes, uintptr_
   h->int8fmt = p->spin_format == SG_INT8;
   const int T = p->n_temps, d = p->ndim;
   h->global = false;
+  h->pair_on = true;
   if (!choose_resident(h, max_dyn_smem())) {
     if (h->int8fmt) { // the int8 layout has no streaming path
       delete h;
@@ -671,10 +674,21 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
   // of leaving the long ones to run on alone at the end of every launch.
   int prio_least = 0, prio_greatest = 0;
   if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_least = prio_greatest = 0;
+  const int smem_limit = max_dyn_smem();
+  // words per CTA of the jobs whose fused sweeps pair their chains' last words (0: not
+  // paired), with that launch's threads and shared memory
+  std::vector<int> pair_w((size_t)n_handles, 0), pair_nt((size_t)n_handles, 0);
+  std::vector<size_t> pair_sm((size_t)n_handles, 0);
+  for (int i = 0; i < n_handles; ++i) {
+    const sg_handle *h = handles[i];
+    pair_nt[i] = h->nt;
+    if (h->pair_on && h->fuse_pt && !h->int8fmt && !h->global && !h->gauss && !h->p.houdayer)
+      pair_w[i] = pair_words(h->job, &pair_nt[i], smem_limit, &pair_sm[i]);
+  }
   std::vector<double> item_work((size_t)n_handles, 0.0);
   for (int i = 0; i < n_handles; ++i) {
     const sg_handle *h = handles[i];
-    const int wpc = h->global ? 1 : h->wpc;
+    const int wpc = pair_w[i] ? pair_w[i] : (h->global ? 1 : h->wpc);
     item_work[i] = (double)h->job.g.N * wpc * (h->fuse_pt ? 1.0 : 2.0);
   }
   std::vector<double> ranked = item_work;
@@ -712,7 +726,8 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
     for (size_t gi = 0; gi < groups.size(); ++gi) {
       const sg_handle *o = handles[groups[gi][0]];
       if (o->job.g.d == h->job.g.d && o->job.g.L0 == h->job.g.L0 && o->job.g.L1 == h->job.g.L1 &&
-          o->job.g.L2 == h->job.g.L2 && o->job.Wc == h->job.Wc) {
+          o->job.g.L2 == h->job.g.L2 && o->job.Wc == h->job.Wc && pair_w[groups[gi][0]] == pair_w[i] &&
+          pair_nt[groups[gi][0]] == pair_nt[i]) {
         group_of[i] = (int)gi;
         groups[gi].push_back(i);
         break;
@@ -730,21 +745,25 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
     p0.push_back(h->t_pt);
     h0.push_back(h->t_houd);
   }
-  const int smem_limit = max_dyn_smem();
   for (size_t gi = 0; gi < groups.size() && r == SG_OK && e == cudaSuccess; ++gi) {
     cudaStream_t q = b->streams[groups[gi][0]];
     e = cudaStreamWaitEvent(q, b->events[0], 0);
     // one shape for the group: the first job's (tuned) shape, falling back to one word
-    // per CTA when a job has an odd number of words or two do not fit
+    // per CTA when a job has an odd number of words or two do not fit; a group of paired
+    // jobs holds a whole sample per CTA
     sg_handle *lead = handles[groups[gi][0]];
-    int wpc = lead->wpc;
-    size_t sm = 0;
-    for (int i : groups[gi])
-      if (handles[i]->job.W % wpc) wpc = 1;
-    if (wpc == 2 && !packed_shape_ok(lead, lead->nt, 2, smem_limit, &sm)) wpc = 1;
-    if (!packed_shape_ok(lead, lead->nt, wpc, smem_limit, &sm)) {
-      r = SG_EUNSUPPORTED;
-      break;
+    const int pw = pair_w[groups[gi][0]];
+    int wpc = pw ? pw : lead->wpc;
+    int nt = pw ? pair_nt[groups[gi][0]] : lead->nt;
+    size_t sm = pw ? pair_sm[groups[gi][0]] : 0;
+    if (!pw) {
+      for (int i : groups[gi])
+        if (handles[i]->job.W % wpc) wpc = 1;
+      if (wpc == 2 && !packed_shape_ok(lead, lead->nt, 2, smem_limit, &sm)) wpc = 1;
+      if (!packed_shape_ok(lead, lead->nt, wpc, smem_limit, &sm)) {
+        r = SG_EUNSUPPORTED;
+        break;
+      }
     }
     std::vector<JobDesc> descs;
     std::vector<sg_handle *> unfused;
@@ -754,8 +773,8 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
       jd.jb = h->job;
       jd.dv = h->dev;
       jd.first_item = 0;
-      jd.n_items = h->job.S * (h->job.W / wpc);
-      jd.fuse = (wpc % h->job.Wc == 0) ? 1 : 0;
+      jd.n_items = pw ? h->job.S : h->job.S * (h->job.W / wpc);
+      jd.fuse = (pw || wpc % h->job.Wc == 0) ? 1 : 0;
       jd.n_metro = h->p.n_metro;
       descs.push_back(jd);
       if (!jd.fuse) unfused.push_back(h);
@@ -765,7 +784,7 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
     // launch for all their jobs
     const int chunk = unfused.empty() ? mcs_per_launch : 1;
     for (int m = 0; m < mcs_per_launch && e == cudaSuccess; m += chunk) {
-      e = launch_resident_batch(descs.data(), (int)descs.size(), lead->nt, wpc, sm, q, chunk);
+      e = launch_resident_batch(descs.data(), (int)descs.size(), nt, wpc, sm, q, chunk, pw != 0);
       if (e == cudaSuccess && !unfused.empty()) e = launch_exchange_batch(descs.data(), (int)descs.size(), q);
     }
     for (int i : groups[gi]) {
@@ -1081,6 +1100,12 @@ sg_status sg_set_launch(sg_handle *h, int32_t threads, int32_t words) {
   h->smem = sm;
   h->global = false;
   h->fuse_pt = wpc % h->job.Wc == 0;
+  return SG_OK;
+}
+
+sg_status sg_set_pairing(sg_handle *h, int32_t on) {
+  if (!h || (on != 0 && on != 1)) return SG_EINVAL;
+  h->pair_on = on != 0;
   return SG_OK;
 }
 

@@ -161,6 +161,8 @@ struct ResidentParams {
   JobDesc jobs[MAXJ];
 };
 constexpr int MAX_BATCH_JOBS = 96;
+using resident_fn1 = void (*)(ResidentParams<1>);
+using resident_fnB = void (*)(ResidentParams<MAX_BATCH_JOBS>);
 
 // ---------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64
@@ -390,7 +392,9 @@ constexpr int PT_WORDS = 6 * 64 + 8;
 struct PackedSmem {
   int spin, jbyte, jpl, thr, epart, pt, bar, total;
 };
-__host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthreads, int wpc) {
+// chains: the chain slots of the exchange state (default one per word; two when a CTA
+// pairs the two chains' partial words of a sample).
+__host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthreads, int wpc, int chains = 0) {
   PackedSmem L;
   L.spin = 0;
   L.jbyte = L.spin + 4 * N * wpc;
@@ -398,7 +402,7 @@ __host__ __device__ inline PackedSmem packed_smem(int N, int NW, int d, int nthr
   L.thr = L.jpl + round16(4 * d * NW);
   L.epart = L.thr + wpc * 256 * 8; // lane-pair threshold tables, 16 pairs x 16 codes x 8 bytes
   L.pt = L.epart + 4 * nthreads * wpc;
-  L.bar = L.pt + round16(4 * PT_WORDS * wpc);
+  L.bar = L.pt + round16(4 * PT_WORDS * (chains > 0 ? chains : wpc));
   L.total = L.bar + 16;
   return L;
 }
@@ -435,12 +439,21 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
                             int32_t *meas_E = nullptr, int32_t *meas_Q = nullptr, bool after_move = false,
-                            const HoudMaps *hm = nullptr, int houd = 0);
+                            const HoudMaps *hm = nullptr, int houd = 0, bool allow_pair = false);
 // Several jobs of the same lattice shape in one launch (chunks of MAX_BATCH_JOBS).
 // jobs[i].n_items/fuse/n_metro must be filled; first_item is set here.
 cudaError_t launch_resident_batch(JobDesc *jobs, int n_jobs, int nthreads, int wpc, size_t smem, cudaStream_t st,
-                                  int n_mcs);
+                                  int n_mcs, bool pair = false);
 cudaError_t launch_exchange(const Job &jb, const Dev &dv, cudaStream_t st);
+// Paired last words (k_metro_pair.cu): the words per CTA (1: two chains of T <= 16 in one
+// word; 3: two chains of 33..48 replicas, their full first words and one paired word) of
+// a two-chain job whose sweeps run with the exchange fused, or 0 where pairing does not
+// apply.  *nthreads is raised to the smallest CTA that has a warp per word and
+// *smem set to the launch's shared memory, which must fit smem_limit.
+int pair_words(const Job &jb, int *nthreads, int smem_limit, size_t *smem);
+resident_fn1 pair_kernel_1(int d, int nthreads, int wpc);
+resident_fnB pair_kernel_batch(int d, int nthreads, int wpc);
+cudaError_t prepare_pair_kernels(int max_smem);
 cudaError_t launch_exchange_batch(JobDesc *jobs, int n_jobs, cudaStream_t st);
 cudaError_t prepare_resident_kernels(int max_smem);
 cudaError_t prepare_houdayer_kernels(int max_smem);

@@ -314,17 +314,90 @@ __device__ __forceinline__ uint32_t decide_site(const SiteCount<D> &cnt, const P
   return cnt.aut | ~rej;
 }
 
+// K calls for each of two counter bases, interleaved round by round (2K chains): out[u] is
+// the call with c3 = c3lo | u << 8 and out[K + u] the one with c3hi | u << 8, u < K.
+template <int K>
+__device__ __forceinline__ void philox_finish2K(const PhiloxSweep &P, const PhiloxSite &Q, uint32_t c3lo,
+                                                uint32_t c3hi, const Job &jb, uint4 (&out)[2 * K]) {
+  uint32_t a0[2 * K], a1[2 * K], a2[2 * K], a3[2 * K];
+#pragma unroll
+  for (int u = 0; u < 2 * K; ++u) {
+    const uint32_t c3 = (u < K ? c3lo : c3hi) | ((uint32_t)(u < K ? u : u - K) << 8);
+    const uint32_t y = Q.X ^ c3;
+    uint32_t h, l;
+    mulwide(PH_M1, y, h, l);
+    const uint32_t z0 = h ^ P.B ^ jb.rk0[1];
+    uint32_t ph, pl;
+    mulwide(PH_M0, z0, ph, pl);
+    a0[u] = Q.hiZ ^ l ^ jb.rk0[2];
+    a1[u] = Q.loZ;
+    a2[u] = ph ^ Q.z3 ^ jb.rk1[2];
+    a3[u] = pl;
+  }
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+#pragma unroll
+    for (int u = 0; u < 2 * K; ++u) {
+      uint32_t h0, l0, h1, l1;
+      mulwide(PH_M0, a0[u], h0, l0);
+      mulwide(PH_M1, a2[u], h1, l1);
+      const uint32_t n0 = h1 ^ a1[u] ^ jb.rk0[r], n2 = h0 ^ a3[u] ^ jb.rk1[r];
+      a0[u] = n0; a1[u] = l1; a2[u] = n2; a3[u] = l0;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2 * K; ++u) out[u] = make_uint4(a0[u], a1[u], a2[u], a3[u]);
+}
+
+// Metropolis decisions of a paired word: lanes 0..15 hold replicas of chain 0 and lanes
+// 16..31 the same replicas of chain 1 (the two chains' last, partial words), each half
+// with K groups of 4 in use.  Group u < 4 draws chain 0's word with c3 = c3lo | u << 8,
+// group 4 + u chain 1's with c3lo | 1 << 20 | u << 8: exactly the words the two
+// unpaired partial words would draw.  Returns the accepted-flip mask.
+template <int D, int K>
+__device__ __forceinline__ uint32_t decide_pair_k(const SiteCount<D> &cnt, const PhiloxSweep &P,
+                                                  const PhiloxSite &Q, uint32_t c3lo,
+                                                  const uint2 *__restrict__ pair_tab, const Job &jb) {
+  uint4 rr[2 * K];
+  philox_finish2K<K>(P, Q, c3lo, c3lo | (1u << 20), jb, rr);
+  uint32_t rej = 0;
+#pragma unroll
+  for (int u = 7; u >= 4; --u) {
+    if (u - 4 < K) rej = decide_group<D>(rej, rr[K + u - 4], u, cnt, pair_tab);
+    else rej <<= 4;
+  }
+#pragma unroll
+  for (int u = 3; u >= 0; --u) {
+    if (u < K) rej = decide_group<D>(rej, rr[u], u, cnt, pair_tab);
+    else rej <<= 4;
+  }
+  return cnt.aut | ~rej;
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t decide_pair(const SiteCount<D> &cnt, const PhiloxSweep &P,
+                                                const PhiloxSite &Q, uint32_t c3lo, int ngroups,
+                                                const uint2 *__restrict__ pair_tab, const Job &jb) {
+  switch (ngroups) {
+  case 1: return decide_pair_k<D, 1>(cnt, P, Q, c3lo, pair_tab, jb);
+  case 2: return decide_pair_k<D, 2>(cnt, P, Q, c3lo, pair_tab, jb);
+  case 3: return decide_pair_k<D, 3>(cnt, P, Q, c3lo, pair_tab, jb);
+  default: return decide_pair_k<D, 4>(cnt, P, Q, c3lo, pair_tab, jb);
+  }
+}
+
 // Fill the pair tables of one word from its lanes' temperature slots (one warp; lane
 // j's slot in kslot).  Entry (pair p, code) = (thr of lane 2p for u = u0a + 2 u1a,
 // thr of lane 2p+1 for u = u0b + 2 u1b), code = u0a | u0b << 1 | u1a << 2 | u1b << 3.
 // In 2D only the low bit of u selects (u >= 2 is auto-accepted).
 template <int D>
-__device__ __forceinline__ void fill_pair_table(uint2 *pair_tab, int lane, int kslot, int nvalid,
+__device__ __forceinline__ void fill_pair_table(uint2 *pair_tab, int lane, int kslot, bool valid,
                                                 const uint32_t *thr) {
-  // this lane's four thresholds by u = 0..3 (m = d - u for u < d; 0 otherwise)
+  // this lane's four thresholds by u = 0..3 (m = d - u for u < d; 0 otherwise or for a
+  // lane that holds no replica)
   uint32_t mine[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) mine[u] = (lane < nvalid && u < D) ? thr[kslot * 4 + (D - u)] : 0u;
+  for (int u = 0; u < 4; ++u) mine[u] = (valid && u < D) ? thr[kslot * 4 + (D - u)] : 0u;
   // 256 entries: lane handles pair (lane / 2) ... every (pair, code) via shuffles
 #pragma unroll
   for (int rep = 0; rep < 8; ++rep) {

@@ -55,7 +55,7 @@ EXPORTED = (
     "sg_measure", "sg_measure_device", "sg_measure_async", "sg_measure_wait", "sg_run_mcs_measure_async", "sg_measure_qmodes", "sg_measure_qmodes_device", "sg_trips",
     "sg_import_couplings_fixed", "sg_measure64", "sg_get_state64", "sg_checkpoint_bytes", "sg_checkpoint",
     "sg_restore", "sg_selftest_wait", "sg_export_spins", "sg_import_spins", "sg_export_couplings", "sg_import_couplings",
-    "sg_get_state", "sg_counters", "sg_exact_path_counters", "sg_thresholds", "sg_set_launch", "sg_get_launch", "sg_batch_create",
+    "sg_get_state", "sg_counters", "sg_exact_path_counters", "sg_thresholds", "sg_set_launch", "sg_set_pairing", "sg_get_launch", "sg_batch_create",
     "sg_batch_run", "sg_batch_destroy", "sg_sweep_streaming_static", "sg_probe_philox", "sg_destroy",
     "sg_strerror",
 )
@@ -106,6 +106,7 @@ def lib():
         "sg_exact_path_counters": [P, P, P, U],
         "sg_thresholds": [P, P],
         "sg_set_launch": [P, I32, I32],
+        "sg_set_pairing": [P, I32],
         "sg_get_launch": [P, P, P, P],
         "sg_batch_create": [P, I32, I32, U, ctypes.POINTER(P)],
         "sg_batch_run": [P, I32, U],
@@ -414,6 +415,11 @@ class Simulation:
         """Resident-kernel launch shape (threads per CTA, words per CTA); results are
         identical for every accepted shape."""
         _check(lib().sg_set_launch(self._h, int(threads), int(words)), "sg_set_launch")
+
+    def set_pairing(self, on: bool = True):
+        """Allow (default) or forbid pairing the two chains' partial last words in one
+        word in the fused MCS; the results are identical either way."""
+        _check(lib().sg_set_pairing(self._h, 1 if on else 0), "sg_set_pairing")
 
     def launch(self):
         v = np.zeros(3, np.int32)
