@@ -537,6 +537,15 @@ bool multi_possible(const sg_handle *h) {
   return houdayer_possible(&h->p, h->job) && h->lay.houd_bytes > 0 && houdayer_labels(h->job);
 }
 
+// The words per CTA when this handle's fused MCS pairs its chains' last words (0: it
+// does not).  Pairing holds whole chains, so it applies whatever the handle's own shape.
+int pair_ok(const sg_handle *h) {
+  if (!h->pair_on || h->int8fmt || h->global || h->gauss || h->p.houdayer) return 0;
+  int nt = h->nt;
+  size_t sm = 0;
+  return pair_words(h->job, &nt, max_dyn_smem(), &sm);
+}
+
 // Whether an MCS with the move can give its first and last phases to the resident
 // launches around it: packed spins in shared memory, one CTA per sample holding both
 // one-word chains, the bitmap scratch present, the exchange fused.
@@ -562,7 +571,7 @@ namespace {
 sg_status mcs_ops(sg_handle *h, int n_mcs, cudaStream_t st) {
   if (n_mcs == 0) return SG_OK;
   const int nm = h->p.n_metro;
-  if (!h->p.houdayer && h->fuse_pt && !h->global) {
+  if (!h->p.houdayer && !h->global && (h->fuse_pt || pair_ok(h))) {
     sg_status r = launch_resident<true, false>(h, st, n_mcs, nm);
     if (r == SG_OK) {
       h->t_metro += (uint64_t)n_mcs * (uint64_t)nm;
@@ -682,14 +691,14 @@ sg_status sg_batch_create(sg_handle *const *handles, int32_t n_handles, int32_t 
   for (int i = 0; i < n_handles; ++i) {
     const sg_handle *h = handles[i];
     pair_nt[i] = h->nt;
-    if (h->pair_on && h->fuse_pt && !h->int8fmt && !h->global && !h->gauss && !h->p.houdayer)
+    if (h->pair_on && !h->int8fmt && !h->global && !h->gauss && !h->p.houdayer)
       pair_w[i] = pair_words(h->job, &pair_nt[i], smem_limit, &pair_sm[i]);
   }
   std::vector<double> item_work((size_t)n_handles, 0.0);
   for (int i = 0; i < n_handles; ++i) {
     const sg_handle *h = handles[i];
     const int wpc = pair_w[i] ? pair_w[i] : (h->global ? 1 : h->wpc);
-    item_work[i] = (double)h->job.g.N * wpc * (h->fuse_pt ? 1.0 : 2.0);
+    item_work[i] = (double)h->job.g.N * wpc * (h->fuse_pt || pair_w[i] ? 1.0 : 2.0);
   }
   std::vector<double> ranked = item_work;
   std::sort(ranked.begin(), ranked.end());
