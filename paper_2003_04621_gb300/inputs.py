@@ -109,6 +109,13 @@ def workload_3d_l16() -> Workload:
                     geometric_temps(0.9, 2.0, 32), n_mcs=10000)
 
 
+def workload_3d_l16_t40() -> Workload:
+    """The 3D L=16 job with 40 temperatures per chain (two words per chain, the second
+    holding 8 replicas): the case the paired last words serve."""
+    return Workload("3d_L16_S1024_T40_packed", 3, (16, 16, 16), 1024, 2,
+                    geometric_temps(0.9, 2.0, 40), n_mcs=10000)
+
+
 def workload_2d_l128_houdayer() -> Workload:
     """2D +-J L=128, 256 samples x 2 chains x 24 geometric temps in [0.2, 1.6],
     Metropolis + Houdayer + PT each MCS, 5000 MCS."""
