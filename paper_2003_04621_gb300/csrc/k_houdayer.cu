@@ -70,10 +70,11 @@ __device__ __forceinline__ void houd_qmaps(const Job &jb, int RW, const uint32_t
                                            uint32_t *Mc) {
   const int T = jb.T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t tmask = houd_pair_mask(jb, slot0);
+  const BlockMap bm = block_map(jb.g, RW);
   uint32_t mpart = 0u;
   for (int b = warp; b < NBW; b += nwarps) {
     bool valid;
-    const int p = block_site(jb.g, RW, b, lane, valid);
+    const int p = block_site(jb.g, bm, b, lane, valid);
     uint32_t qa = 0u;
     if (valid) qa = (w0p[p] ^ permute_word(sig, w1p[p])) & tmask;
     const uint32_t col = transpose32(qa, lane); // lane a: bit l = q of pair a at site l
@@ -213,12 +214,13 @@ __device__ __forceinline__ void houd_flips(const Job &jb, int RW, const uint32_t
                                            const uint32_t *sigi, uint32_t *w0w, uint32_t *w1w) {
   const int T = jb.T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool mine = lane < T && !((skip >> lane) & 1u);
+  const BlockMap bm = block_map(jb.g, RW);
   for (int b = warp; b < NBW; b += nwarps) {
     const uint32_t cw = mine ? Cb[(size_t)lane * NBW + b] : 0u;
     if (!__any_sync(FULLM, cw != 0u)) continue;
     const uint32_t f0 = transpose32(cw, lane); // lane l: bit a = site l in pair a's cluster
     bool valid;
-    const int p = block_site(jb.g, RW, b, lane, valid);
+    const int p = block_site(jb.g, bm, b, lane, valid);
     if (valid && f0) {
       w0w[p] ^= f0;
       w1w[p] ^= permute_word(sigi, f0);
@@ -337,6 +339,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_q(Job jb, Dev dv, HoudSplit 
   const uint32_t *w1p = dv.spins + ((size_t)s * jb.W + 1) * jb.g.N;
   uint32_t *Qb = hs.Qg + (size_t)s * T * NBW;
   const uint32_t tmask = houd_pair_mask(jb, maps[2]);
+  const BlockMap bm = block_map(jb.g, RW);
   uint32_t mpart = 0u;
   for (int tb = blockIdx.y * HQ_TB; tb < NBW; tb += gridDim.y * HQ_TB) {
     const int nb = min(HQ_TB, NBW - tb);
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_q(Job jb, Dev dv, HoudSplit 
         x0[u] = x1[u] = 0u;
         if (j < nb) {
           bool valid;
-          const int p = block_site(jb.g, RW, tb + j, lane, valid);
+          const int p = block_site(jb.g, bm, tb + j, lane, valid);
           if (valid) {
             x0[u] = w0p[p];
             x1[u] = w1p[p];
@@ -455,6 +458,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_flip(Job jb, Dev dv, HoudSpl
   uint32_t *w0w = dv.spins + ((size_t)s * jb.W + 0) * jb.g.N;
   uint32_t *w1w = dv.spins + ((size_t)s * jb.W + 1) * jb.g.N;
   const uint32_t *Cb = hs.Cg + (size_t)s * T * NBW;
+  const BlockMap bm = block_map(jb.g, RW);
   for (int tb = blockIdx.y * HQ_TB; tb < NBW; tb += gridDim.y * HQ_TB) {
     const int nb = min(HQ_TB, NBW - tb);
     for (int e = tid; e < T * nb; e += HSPLIT_NT) {
@@ -475,7 +479,7 @@ __global__ void __launch_bounds__(HSPLIT_NT) k_houd_flip(Job jb, Dev dv, HoudSpl
           if (__any_sync(FULLM, cw != 0u)) {
             f[u] = transpose32(cw, lane); // lane l: bit a = site l in pair a's cluster
             bool valid;
-            const int p = block_site(jb.g, RW, tb + j, lane, valid);
+            const int p = block_site(jb.g, bm, tb + j, lane, valid);
             if (valid && f[u]) pp[u] = p;
           }
         }

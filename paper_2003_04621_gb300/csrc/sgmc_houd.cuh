@@ -94,12 +94,30 @@ __device__ __forceinline__ void close_row(const uint32_t (&Q)[RW], const uint32_
   }
 }
 
-// Canonical site of bitmap block b, lane l (row r = b / RW, x = 32 (b % RW) + l) as a
-// colour-split index p; `valid` is false for the padding bits past L0.
-__device__ __forceinline__ int block_site(const Geo &g, int RW, int b, int l, bool &valid) {
-  const int r = b / RW, x = 32 * (b - r * RW) + l;
+// Bitmap block b of a pair (row r = b / RW, x = 32 (b % RW) + l for lane l) as a site:
+// the divisions by RW and L1 are multiply-highs with ceil(2^32 / divisor) (division by an
+// invariant integer, Granlund and Montgomery), exact while dividend x divisor < 2^32:
+// the move is limited to L0 <= 256 (RW <= 8) and R <= 65535 rows, so b RW < 2^22 and
+// r L1 <= R^2 < 2^32.
+struct BlockMap {
+  int RW;
+  uint32_t mRW, mL1;
+};
+__device__ __forceinline__ BlockMap block_map(const Geo &g, int RW) {
+  BlockMap bm;
+  bm.RW = RW;
+  bm.mRW = RW > 1 ? 0xFFFFFFFFu / (uint32_t)RW + 1u : 0u;
+  bm.mL1 = g.L1 > 1 ? 0xFFFFFFFFu / (uint32_t)g.L1 + 1u : 0u;
+  return bm;
+}
+// The colour-split index p of block b, lane l; `valid` is false for the padding bits
+// past L0.
+__device__ __forceinline__ int block_site(const Geo &g, const BlockMap &bm, int b, int l, bool &valid) {
+  const int r = bm.RW > 1 ? (int)__umulhi((uint32_t)b, bm.mRW) : b;
+  const int x = 32 * (b - r * bm.RW) + l;
   valid = x < g.L0;
-  const int y = r % g.L1, z = r / g.L1;
+  const int z = g.L1 > 1 ? (int)__umulhi((uint32_t)r, bm.mL1) : r;
+  const int y = r - z * g.L1;
   const int c = (x + y + z) & 1;
   return c * g.Nh + r * g.H + (x >> 1);
 }

@@ -453,6 +453,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     // a warp takes 4 consecutive blocks at a time: lane a loads them as one 16-byte word
     // of pair a's bitmap (bitmaps of a multiple of 4 words; one block at a time otherwise)
     const int G = NBW % 4 == 0 ? 4 : 1;
+    const BlockMap bm = block_map(g, RW);
     for (int b0 = warp * G; b0 < NBW; b0 += (NT / 32) * G) {
       uint32_t cw[4] = {0u, 0u, 0u, 0u};
       if (mine) {
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         if (u < G && __any_sync(FULL, cw[u] != 0u)) {
           const uint32_t f = transpose32(cw[u], lane);
           bool valid;
-          const int p = block_site(g, RW, b0 + u, lane, valid);
+          const int p = block_site(g, bm, b0 + u, lane, valid);
           if (valid && f) {
             sp[p] ^= f;
             sp[g.N + p] ^= permute_word(sigi, f);
@@ -679,6 +680,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     // a warp takes 4 consecutive blocks at a time: lane a stores them as one 16-byte word
     // of pair a's bitmap (bitmaps of a multiple of 4 words; one block at a time otherwise)
     const int G = NBW % 4 == 0 ? 4 : 1;
+    const BlockMap bm = block_map(g, RW);
     for (int b0 = warp * G; b0 < NBW; b0 += (NT / 32) * G) {
       uint32_t col[4];
 #pragma unroll
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         col[u] = 0u;
         if (u < G) {
           bool valid;
-          const int p = block_site(g, RW, b0 + u, lane, valid);
+          const int p = block_site(g, bm, b0 + u, lane, valid);
           const uint32_t qa = valid ? (sp[p] ^ permute_word(sig, sp[g.N + p])) & tmask : 0u;
           col[u] = transpose32(qa, lane); // lane a: bit l = q of pair a at site l
         }
