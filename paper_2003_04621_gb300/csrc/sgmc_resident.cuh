@@ -568,9 +568,10 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
             *TSUM(warp) += sum_add;
           }
         }
+        // the tables follow the new slots, unless this was the launch's last MCS
         if (PAIR) {
-          if (WPC == 3) fill_pair_table<D>(pair_tab + warp * 256, lane, SL(warp)[lane], true, dv.thr);
-        } else if (!ENERGY_ONLY) {
+          if (WPC == 3 && m + 1 < n_outer) fill_pair_table<D>(pair_tab + warp * 256, lane, SL(warp)[lane], true, dv.thr);
+        } else if (!ENERGY_ONLY && m + 1 < n_outer) {
           for (int wc = 0; wc < jb.Wc; ++wc) {
             const int nv = min(32, jb.T - wc * 32);
             fill_pair_table<D>(pair_tab + (warp * jb.Wc + wc) * 256, lane,
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         }
       }
       __syncthreads();
-      if (PAIR) { // the paired word's table needs both chains' new slots
+      if (PAIR && m + 1 < n_outer) { // the paired word's table needs both chains' new slots
         if (warp == WPC - 1) fill_paired();
         __syncthreads();
       }
