@@ -20,7 +20,9 @@ def _built():
 
 
 CASES = [(3, (8, 8, 8), 4), (3, (8, 6, 4), 9), (3, (8, 8, 8), 16), (2, (16, 12), 13), (3, (8, 8, 8), 33),
-         (3, (6, 8, 4), 38), (3, (8, 8, 8), 44), (2, (16, 16), 48), (2, (12, 8), 36)]
+         (3, (6, 8, 4), 38), (3, (8, 8, 8), 44), (2, (16, 16), 48), (2, (12, 8), 36),
+         # lattices smaller than a CTA's threads
+         (2, (2, 8), 8), (2, (8, 2), 14), (3, (4, 6, 2), 36), (3, (2, 2, 2), 40)]
 
 
 @pytest.mark.parametrize("ndim,dims,T", CASES)
@@ -36,7 +38,7 @@ def test_paired_mcs_equals_oracle(oracle_mod, ndim, dims, T):
 
 
 @pytest.mark.parametrize("T", [12, 16, 40, 48])
-@pytest.mark.parametrize("shape", [(128, 2), (256, 1), (512, 2)])
+@pytest.mark.parametrize("shape", [(64, 2), (128, 2), (256, 1), (512, 2)])
 def test_paired_equals_unpaired(T, shape):
     """The same job with pairing allowed and forbidden, on several launch shapes: spins,
     energies, maps, round trips and exchange counts identical after 7 MCS."""
