@@ -87,3 +87,34 @@ def test_pairing_switch_refuses_other_values():
     sim = gpu_of(ndim=2, dims=(8, 8), n_samples=1, n_chains=2, temps=[1.0, 2.0])
     assert lib().sg_set_pairing(sim._h, 2) == 1
     assert lib().sg_set_pairing(sim._h, 0) == 0
+
+
+@pytest.mark.parametrize("T", [10, 42])
+def test_paired_with_several_sweeps_per_mcs(oracle_mod, T):
+    """n_metro = 3 Metropolis sweeps per exchange inside the paired launch."""
+    kw = dict(ndim=3, dims=(8, 4, 6), n_samples=2, n_chains=2, temps=geometric_temps(0.5, 1.8, T), sim_seed=9,
+              n_metro=3)
+    sim = gpu_of(**kw)
+    orc = oracle_of(oracle_mod, **{k: v for k, v in kw.items() if k != "n_metro"})
+    for t in range(3):
+        sim.run_mcs(2)
+        orc.mcs(2, n_metro=3)
+        assert_same_state(sim, orc, f"T={T} step {t}")
+
+
+def test_paired_checkpoint_resume():
+    """A paired job checkpointed and restored into a fresh handle continues exactly."""
+    kw = dict(ndim=3, dims=(8, 8, 8), n_samples=3, n_chains=2, temps=geometric_temps(0.9, 2.0, 44), sim_seed=4,
+              track_trips=True)
+    a = gpu_of(**kw)
+    a.run_mcs(3)
+    blob = a.checkpoint()
+    a.run_mcs(4)
+    b = gpu_of(**kw)
+    b.restore(blob)
+    b.run_mcs(4)
+    np.testing.assert_array_equal(a.spins().cpu().numpy(), b.spins().cpu().numpy())
+    for x, y in zip(a.state()[:2], b.state()[:2]):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(a.trips(), b.trips()):
+        np.testing.assert_array_equal(x, y)
