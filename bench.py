@@ -312,7 +312,7 @@ def bench_batched(stream, steps: int, mcs_per_launch: int = 10, warmup: int = 1)
                       "groups in parallel"}
 
 
-EXTENSIONS = ("houdayer", "gauss", "trips", "houdayer3d", "smalljob")
+EXTENSIONS = ("houdayer", "gauss", "trips", "houdayer3d", "smalljob", "pairing")
 
 
 def _inputs():
@@ -334,7 +334,8 @@ def bench_extensions(stream, steps: int = 5, only=None):
     the 2D L=128 Houdayer MCS with the single-cluster move and with the multi-cluster
     variant; the 2D L=16 Gaussian-coupling MCS; one overlap plane-sum measurement of the
     3D L=16 job; the 3D L=16 MCS with round-trip counting on and off, and with the
-    cluster move on its 8 lowest temperature slots; Metropolis sweeps alone."""
+    cluster move on its 8 lowest temperature slots; Metropolis sweeps alone; the 3D L=16
+    job with 40 temperatures with and without paired last words."""
     import torch
 
     from paper_2003_04621_gb300.inputs import workload_2d_l128_houdayer, workload_3d_l16
@@ -411,6 +412,20 @@ def bench_extensions(stream, steps: int = 5, only=None):
             out[f"houdayer_3d_l16_low{K}" if K < u.T else "houdayer_3d_l16_all"] = {
                 "ms_per_mcs": ms, "attempts_per_ns": u.attempts_per_sweep / (ms * 1e6),
                 "workload": u.name + (f"_houdayer_slots{K}" if K < u.T else "_houdayer_all_slots")}
+            sim.close()
+    # paired last words: the 3D L=16 job with 40 temperatures per chain, paired and not
+    if "pairing" in want:
+        from paper_2003_04621_gb300.inputs import workload_3d_l16_t40
+
+        w40 = workload_3d_l16_t40()
+        for on in (True, False):
+            sim = Simulation(3, w40.dims, w40.n_samples, 2, list(w40.temps), stream=stream)
+            sim.set_launch(256, 2)
+            sim.set_pairing(on)
+            ms = timed(lambda n: sim.run_mcs(n, stream=stream), steps)
+            out["t40_paired" if on else "t40_unpaired"] = {"ms_per_mcs": ms,
+                                                          "attempts_per_ns": w40.attempts_per_sweep / (ms * 1e6),
+                                                          "workload": w40.name}
             sim.close()
     return out
 
