@@ -451,28 +451,38 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     const uint32_t *Cb = rp.hm.Cg + (size_t)s * T * NBW + (size_t)lane * NBW;
     __syncthreads();
     // a warp takes 4 consecutive blocks at a time: lane a loads them as one 16-byte word
-    // of pair a's bitmap (bitmaps of a multiple of 4 words; one block at a time otherwise)
+    // of pair a's bitmap (bitmaps of a multiple of 4 words; one block at a time otherwise),
+    // and issues the loads of BQ such groups before it uses any
     const int G = NBW % 4 == 0 ? 4 : 1;
     const BlockMap bm = block_map(g, RW);
-    for (int b0 = warp * G; b0 < NBW; b0 += (NT / 32) * G) {
-      uint32_t cw[4] = {0u, 0u, 0u, 0u};
-      if (mine) {
-        if (G == 4) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(Cb + b0);
-          cw[0] = v.x, cw[1] = v.y, cw[2] = v.z, cw[3] = v.w;
-        } else {
-          cw[0] = Cb[b0];
+    constexpr int BQ = 4;
+    const int gstep = (NT / 32) * G;
+    for (int base = warp * G; base < NBW; base += BQ * gstep) {
+      uint4 cv[BQ];
+#pragma unroll
+      for (int j = 0; j < BQ; ++j) {
+        const int b0 = base + j * gstep;
+        cv[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (mine && b0 < NBW) {
+          if (G == 4) cv[j] = *reinterpret_cast<const uint4 *>(Cb + b0);
+          else cv[j].x = Cb[b0];
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (u < G && __any_sync(FULL, cw[u] != 0u)) {
-          const uint32_t f = transpose32(cw[u], lane);
-          bool valid;
-          const int p = block_site(g, bm, b0 + u, lane, valid);
-          if (valid && f) {
-            sp[p] ^= f;
-            sp[g.N + p] ^= permute_word(sigi, f);
+      for (int j = 0; j < BQ; ++j) {
+        const int b0 = base + j * gstep;
+        if (b0 >= NBW) break; // warp-uniform
+        const uint32_t cw[4] = {cv[j].x, cv[j].y, cv[j].z, cv[j].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < G && __any_sync(FULL, cw[u] != 0u)) {
+            const uint32_t f = transpose32(cw[u], lane);
+            bool valid;
+            const int p = block_site(g, bm, b0 + u, lane, valid);
+            if (valid && f) {
+              sp[p] ^= f;
+              sp[g.N + p] ^= permute_word(sigi, f);
+            }
           }
         }
       }
