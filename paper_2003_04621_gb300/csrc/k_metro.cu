@@ -277,7 +277,8 @@ packed_fn<MAXJ> pick_packed_nt(int nt) {
   }
 }
 // the kernels that take a phase of the Houdayer move (two one-word chains per CTA):
-// HOUD 1 the sweeps before it (q bitmaps out), HOUD 2 the energies after it (flips in)
+// HOUD 1 the sweeps before it (q bitmaps out), HOUD 2 the energies after it (flips in),
+// HOUD 3 both around one MCS's sweeps (flips, energies and exchange in; q bitmaps out)
 template <int HOUD, bool FULLW = false>
 packed_fn<1> pick_packed_houd(int d, int nt) {
   constexpr bool EONLY = HOUD == 2;
@@ -349,7 +350,9 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
   if (houd != 0) {
     // a phase of the Houdayer move: the CTA must hold both one-word chains of its sample
     const bool ok = hm && !int8fmt && wpc == 2 && jb.C == 2 && jb.Wc == 1 && !meas &&
-                    (houd == 1 ? !energy_only : (houd == 2 && energy_only && after_move && fuse_pt));
+                    (houd == 1   ? !energy_only
+                     : houd == 2 ? energy_only && after_move && fuse_pt
+                                 : houd == 3 && !energy_only && fuse_pt && n_mcs == 1);
     if (!ok) return cudaErrorInvalidValue;
     rp.hm = *hm;
   } else {
@@ -357,6 +360,8 @@ cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthr
   }
   const packed_fn<1> fn = houd == 1    ? (full ? pick_packed_houd<1, true>(jb.g.d, nthreads)
                                                : pick_packed_houd<1, false>(jb.g.d, nthreads))
+                          : houd == 3  ? (full ? pick_packed_houd<3, true>(jb.g.d, nthreads)
+                                               : pick_packed_houd<3, false>(jb.g.d, nthreads))
                           : houd == 2  ? pick_packed_houd<2>(jb.g.d, nthreads)
                           : meas       ? (full ? pick_packed_meas<true>(jb.g.d, nthreads) : pick_packed_meas<false>(jb.g.d, nthreads))
                           : energy_only ? pick_packed<true, 1>(jb.g.d, nthreads, wpc)
@@ -412,6 +417,8 @@ cudaError_t prepare_resident_kernels(int max_smem) {
           fns.push_back((const void *)pick_packed_houd<1, false>(d, nt));
           fns.push_back((const void *)pick_packed_houd<1, true>(d, nt));
           fns.push_back((const void *)pick_packed_houd<2>(d, nt));
+          fns.push_back((const void *)pick_packed_houd<3, false>(d, nt));
+          fns.push_back((const void *)pick_packed_houd<3, true>(d, nt));
         }
       }
   for (int d = 2; d <= 3; ++d)

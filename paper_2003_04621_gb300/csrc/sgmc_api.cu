@@ -582,22 +582,28 @@ sg_status mcs_ops(sg_handle *h, int n_mcs, cudaStream_t st) {
   if (h->p.houdayer && !houdayer_possible(&h->p, h->job)) return SG_EUNSUPPORTED;
   if (h->p.houdayer == 2 && !multi_possible(h)) return SG_EUNSUPPORTED;
   if (houd_fused(h)) {
-    // the move's q bitmaps come out of the sweep launch and its flips go into the energy
-    // launch, which also runs the exchange: three launches per MCS around the cluster phase
+    // the move's q bitmaps come out of the sweep launch and its flips go into the next
+    // launch: the next MCS's sweep launch, which first takes the energies after the move
+    // and that MCS's exchange (HOUD 3), or after the last MCS one energy launch with the
+    // exchange (HOUD 2).  Two launches per MCS around the cluster phase, and one more
+    // per call.
     const sgmc::HoudMaps hm = sgmc::houd_maps_of(h->job, reinterpret_cast<uint32_t *>(h->buf + h->lay.houd));
     for (int m = 0; m < n_mcs; ++m) {
-      sg_status r = check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, false, false, h->smem, st,
-                                                   nm, 1, nullptr, nullptr, false, &hm, 1));
+      sg_status r =
+          m == 0 ? check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, false, false, h->smem, st, nm,
+                                                  1, nullptr, nullptr, false, &hm, 1))
+                 : check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, true, false, h->smem, st, 1,
+                                                  nm, nullptr, nullptr, false, &hm, 3));
       if (r != SG_OK) return r;
+      if (m > 0) h->t_pt += 1;
       h->t_metro += (uint64_t)nm;
       r = houdayer_move(h, st, h->p.houdayer == 2, true);
       if (r != SG_OK) return r;
-      r = check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, true, true, h->smem, st, 1, 1, nullptr,
-                                         nullptr, true, &hm, 2));
-      if (r != SG_OK) return r;
-      h->t_pt += 1;
     }
-    return SG_OK;
+    const sg_status r = check(h, sgmc::launch_resident(h->job, h->dev, false, h->nt, h->wpc, true, true, h->smem, st,
+                                                       1, 1, nullptr, nullptr, true, &hm, 2));
+    if (r == SG_OK) h->t_pt += 1;
+    return r;
   }
   for (int m = 0; m < n_mcs; ++m) {
     sg_status r = sweeps(h, nm, st);

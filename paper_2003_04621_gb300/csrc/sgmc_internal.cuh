@@ -434,8 +434,10 @@ __host__ __device__ inline Int8Smem int8_smem(int N, int NW, int d, int T, int T
 
 // Host-side launchers (each .cu file keeps its kernels to itself and exposes these).
 // houd = 1: after the last sweep, the Houdayer q bitmaps and M of every pair into *hm;
-// houd = 2 (energy-only after a move): first the cluster flips from *hm.  Both need a CTA
-// that holds both one-word chains of a sample (wpc 2, two chains of T <= 32).
+// houd = 2 (energy-only after a move): first the cluster flips from *hm; houd = 3 (one
+// MCS, fused): first the previous move's flips, the energies after it and the exchange,
+// then the sweeps and the next move's q bitmaps.  All need a CTA that holds both
+// one-word chains of a sample (wpc 2, two chains of T <= 32).
 cudaError_t launch_resident(const Job &jb, const Dev &dv, bool int8fmt, int nthreads, int wpc, bool fuse_pt,
                             bool energy_only, size_t smem, cudaStream_t st, int n_mcs, int n_metro,
                             int32_t *meas_E = nullptr, int32_t *meas_Q = nullptr, bool after_move = false,

@@ -250,7 +250,9 @@ __device__ __forceinline__ void exchange_chain_smem(int T, const double *beta, i
 // replicas), so the partial-word decision code is left out of the instantiation.
 // HOUD (single-job launches whose CTAs hold both one-word chains of a sample): 1, after
 // the last sweep write the Houdayer move's q bitmaps and M of every pair; 2 (energy
-// only, right after the move's cluster phase), first apply the move's cluster flips.
+// only, right after the move's cluster phase), first apply the move's cluster flips;
+// 3 (one MCS of sweeps between two moves), first the previous move's flips, the energies
+// after it and that MCS's exchange, then the sweeps, then the next move's q bitmaps.
 // PAIR (sweeps with the exchange fused, two chains whose last word holds at most 16
 // replicas): a CTA holds one whole sample, the chains' full words (WPC = 3: one each)
 // and ONE paired word whose lanes 0..15 are chain 0's last word and lanes 16..31 chain
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
   };
   __syncthreads(); // the chains' maps
   const bool okj = mbar_wait(bar, 0, MBAR_MAX_TRIES);
-  if (!ENERGY_ONLY && warp < WPC) {
+  if (!ENERGY_ONLY && HOUD != 3 && warp < WPC) { // (HOUD 3: after its exchange)
     if (PAIR) {
       if (warp < WPC - 1) fill_pair_table<D>(pair_tab + warp * 256, lane, SL(warp)[lane], true, dv.thr);
       else fill_paired();
@@ -425,10 +427,37 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       mbar_wait(bar, 0, MBAR_MAX_TRIES);
       mbar_wait(bar + 1, 0, MBAR_MAX_TRIES);
     }
-    job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD == 2 ? 1ull : 0ull);
+    job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD >= 2 ? 1ull : 0ull);
     return;
   }
-  if constexpr (HOUD == 2) {
+  // warp ci < nch: chain ci's exchange pass number t_pt0 + m (Eq. 5), then its round trips
+  auto exchange_step = [&](int m) {
+    exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), PACC(warp), NEAR(warp), EXACT(warp), s_glob,
+                        (uint32_t)(c0 + warp), t_pt0 + (uint32_t)m, jb);
+    if (track) {
+      uint32_t n_add = 0u;
+      unsigned long long sum_add = 0ull;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j < jb.T) {
+          int32_t dir = TD(warp)[j];
+          uint32_t t0 = T0(warp)[j];
+          trip_step(jb.T, SL(warp)[j], dir, t0, t_pt0 + (uint32_t)m + 1u, n_add, sum_add);
+          TD(warp)[j] = dir;
+          T0(warp)[j] = t0;
+        }
+      }
+      n_add = __reduce_add_sync(FULL, n_add);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum_add += __shfl_xor_sync(FULL, sum_add, o);
+      if (lane == 0) {
+        *TN(warp) += n_add;
+        *TSUM(warp) += sum_add;
+      }
+    }
+  };
+  if constexpr (HOUD == 2 || HOUD == 3) {
     // Houdayer move, phase 3 (Eq. 10): on pair a's cluster (chain-0 lane a with the
     // chain-1 lane b = perm1[slot0[a]] of the same slot) both replicas flip.  A warp
     // transposes the pairs' cluster bitmap words of a 32-site block (lane l: bit a = site l
@@ -488,6 +517,39 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       }
     }
     __syncthreads();
+  }
+  if constexpr (HOUD == 3) {
+    // the energies after the previous MCS's move (chain 0's counted, chain 1's from the
+    // pair sums E_a + E_b that the move conserves; the global energies are still those
+    // before it), then that MCS's exchange and the threshold tables of the new slots
+    {
+      uint32_t V[WPC][NB];
+#pragma unroll
+      for (int w = 0; w < WPC; ++w)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) V[w][b] = 0u;
+      const PhiloxSweep P0 = {}; // (counting only: no draws)
+      half_sweep<D, NT, WPC, true, false, false>(g, 1, true, sp, jbyte, pair_tab, vmask, ngroups, c3base, P0, jb, V,
+                                                 1);
+      epart[tid] = warp_lane_sum(V[0]);
+      __syncthreads();
+      if (warp == 0) {
+        int32_t U = 0;
+        for (int wq = 0; wq < NT / 32; ++wq) U += epart[wq * 32 + lane];
+        EL(0)[lane] = 2 * U - D * g.N;
+      }
+      __syncthreads();
+      if (warp == 1 && lane < jb.T) {
+        const size_t cb0 = (size_t)s * 2 * jb.T, cb1 = cb0 + jb.T;
+        const int a = PM(0)[lane], b = PM(1)[lane];
+        EL(1)[b] = dv.E[cb0 + a] + dv.E[cb1 + b] - EL(0)[a];
+      }
+      __syncthreads();
+    }
+    if (warp < 2) {
+      exchange_step(0);
+      fill_pair_table<D>(pair_tab + warp * 256, lane, lane < jb.T ? SL(warp)[lane] : 0, lane < jb.T, dv.thr);
+    }
   }
   // the sweeps start after a full barrier (which also keeps the prologue's values out of
   // the sweep loop's register allocation)
@@ -551,33 +613,10 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
         __syncthreads();
       }
     }
-    if (nch > 0) {
+    if (nch > 0 && HOUD != 3) { // (HOUD 3: the exchange came before the sweeps)
       // warp ci exchanges chain ci, then refreshes the tables of the chain's words
       if (warp < nch) {
-        exchange_chain_smem(jb.T, dv.beta, PM(warp), SL(warp), EL(warp), PACC(warp), NEAR(warp), EXACT(warp), s_glob,
-                            (uint32_t)(c0 + warp), t_pt0 + (uint32_t)m, jb);
-        if (track) {
-          uint32_t n_add = 0u;
-          unsigned long long sum_add = 0ull;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int j = lane + 32 * h;
-            if (j < jb.T) {
-              int32_t dir = TD(warp)[j];
-              uint32_t t0 = T0(warp)[j];
-              trip_step(jb.T, SL(warp)[j], dir, t0, t_pt0 + (uint32_t)m + 1u, n_add, sum_add);
-              TD(warp)[j] = dir;
-              T0(warp)[j] = t0;
-            }
-          }
-          n_add = __reduce_add_sync(FULL, n_add);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sum_add += __shfl_xor_sync(FULL, sum_add, o);
-          if (lane == 0) {
-            *TN(warp) += n_add;
-            *TSUM(warp) += sum_add;
-          }
-        }
+        exchange_step(m);
         // the tables follow the new slots, unless this was the launch's last MCS
         if (PAIR) {
           if (WPC == 3 && m + 1 < n_outer) fill_pair_table<D>(pair_tab + warp * 256, lane, SL(warp)[lane], true, dv.thr);
@@ -656,20 +695,34 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
       if (tid < T) rp.mQ[(size_t)s * T + SL(0)[tid]] = g.N - 2 * (int32_t)tot[tid];
     }
   }
-  if constexpr (HOUD == 1) {
+  if constexpr (HOUD == 1 || HOUD == 3) {
     // Houdayer move, phase 1 (Eq. 10) on the final configurations: per site the chain-1
     // word is permuted lane b -> lane a = perm0[slot1[b]] (byte tables), so that bit a of
     // w0 ^ sigma(w1) is q = -1 of pair a; a warp transposes 32 sites x 32 pairs, giving
     // each pair's bitmap word of the block, and M counts the q = -1 sites of each pair.
-    // Only pairs at a slot below hK take part (the others get an empty bitmap).
+    // Only pairs at a slot below hK take part (the others get an empty bitmap).  The maps
+    // are the global ones (HOUD 1, no exchange in the launch) or the held ones (HOUD 3,
+    // after its exchange).
     __syncthreads(); // every warp is past its last half-sweep: the pair tables are free
-    int32_t *maps = ptw; // perm0, perm1, slot0, slot1 [32 each], then M [32]
-    uint32_t *Mc = reinterpret_cast<uint32_t *>(ptw + 128);
+    const int32_t *perm0, *slot0, *slot1;
+    uint32_t *Mc;
     const int T = jb.T, NBW = rp.hm.NBW, RW = rp.hm.RW;
-    if (warp < 2) {
-      const size_t cb = ((size_t)s * 2 + warp) * T;
-      maps[warp * 32 + lane] = lane < T ? dv.perm[cb + lane] : 0;
-      maps[64 + warp * 32 + lane] = lane < T ? dv.slot[cb + lane] : 0;
+    if (HOUD == 1) {
+      int32_t *maps = ptw; // perm0, perm1, slot0, slot1 [32 each], then M [32]
+      if (warp < 2) {
+        const size_t cb = ((size_t)s * 2 + warp) * T;
+        maps[warp * 32 + lane] = lane < T ? dv.perm[cb + lane] : 0;
+        maps[64 + warp * 32 + lane] = lane < T ? dv.slot[cb + lane] : 0;
+      }
+      perm0 = maps;
+      slot0 = maps + 64;
+      slot1 = maps + 96;
+      Mc = reinterpret_cast<uint32_t *>(ptw + 128);
+    } else {
+      perm0 = PM(0);
+      slot0 = SL(0);
+      slot1 = SL(1);
+      Mc = reinterpret_cast<uint32_t *>(epart);
     }
     if (tid < 32) Mc[tid] = 0u;
     __syncthreads();
@@ -680,11 +733,11 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
 #pragma unroll
       for (int bb = 0; bb < 8; ++bb) {
         const int b = 8 * j + bb;
-        if (((v >> bb) & 1) && b < T) o |= 1u << maps[maps[96 + b]];
+        if (((v >> bb) & 1) && b < T) o |= 1u << perm0[slot1[b]];
       }
       sig[e] = o;
     }
-    const uint32_t tmask = houd_pair_mask(jb, maps + 64);
+    const uint32_t tmask = houd_pair_mask(jb, slot0);
     uint32_t *Qb = rp.hm.Qg + (size_t)s * T * NBW + (size_t)lane * NBW;
     uint32_t mpart = 0u;
     __syncthreads();
@@ -767,7 +820,7 @@ __global__ void __launch_bounds__(NT, SGMC_MIN_THREADS / NT)
     __syncthreads();
     if (tid == 0) bulk_s2g_and_release(gsp, sp, 4u * (uint32_t)(g.N * WPC));
   }
-  job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD == 2 ? 1ull : 0ull);
+  job_done_advance(dv.ctr, JD.n_items, adv_metro, adv_pt, HOUD >= 2 ? 1ull : 0ull);
 }
 
 } // namespace sgmc

@@ -89,7 +89,8 @@ def test_houdayer_mcs_2d_l128(oracle_mod):
 def test_houdayer_mcs_fused_and_split_phases(oracle_mod, multi, ndim, dims, T):
     """The MCS with the move, once with its q bitmaps and flips taken by the resident
     launches around the cluster phase (two one-word chains per CTA), once with the three
-    separate move kernels (one word per CTA): both equal the oracle after every MCS."""
+    separate move kernels (one word per CTA): both equal the oracle after every call, for
+    calls of one and of several MCS."""
     kw = dict(ndim=ndim, dims=dims, n_samples=3, n_chains=2, temps=geometric_temps(0.3, 1.8, T), sim_seed=11,
               coupling_seed=2, houdayer=2 if multi else True)
     states = []
@@ -97,10 +98,12 @@ def test_houdayer_mcs_fused_and_split_phases(oracle_mod, multi, ndim, dims, T):
         sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
         sim.set_launch(256, words)
         assert sim.launch()["words"] == words
-        for t in range(5):
-            sim.run_mcs(1)
-            orc.mcs(1, houdayer=kw["houdayer"])
-            assert_same_state(sim, orc, f"words {words} mcs {t}")
+        # one MCS per call, then several (the fused form then runs the move's flips, the
+        # energies and the exchange inside the next MCS's sweep launch)
+        for t, n in enumerate((1, 1, 3, 2, 4)):
+            sim.run_mcs(n)
+            orc.mcs(n, houdayer=kw["houdayer"])
+            assert_same_state(sim, orc, f"words {words} call {t} ({n} MCS)")
         assert sim.counters()["houdayer_sites"] == orc.counters()["houd_flipped"]
         states.append(sim.spins().cpu().numpy())
     np.testing.assert_array_equal(states[0], states[1])
