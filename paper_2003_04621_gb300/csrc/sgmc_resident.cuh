@@ -2,11 +2,14 @@
 // the energy (Eq. 1) and, when a chain fits in one CTA, the replica exchange (Eq. 5)
 // fused in, as a template that k_metro.cu and k_metro_pair.cu instantiate.
 //
-// Packed kernel: one CTA owns one 32-replica word lattice (sample s, word w) for the
-// whole launch.  TMA bulk-copies the N words and the sample's coupling bit planes into
-// shared memory, runs n_mcs x n_metro checkerboard sweeps there (colour 0 then colour 1,
-// each site updating its 32 replicas at once), keeps the energies exact, optionally
-// performs the chain's exchange pass between MCS, and bulk-copies the lattice back.
+// Packed kernel: one CTA owns WPC 32-replica word lattices of one sample (usually both
+// one-word chains) for the whole launch.  TMA bulk-copies the N words and the sample's
+// coupling bit planes into shared memory, runs n_mcs x n_metro checkerboard sweeps there
+// (colour 0 then colour 1, each site updating its 32 replicas at once), keeps the
+// energies exact, optionally performs the chains' exchange passes between MCS, and
+// bulk-copies the lattice back.  Template flags add the fused measurement (MEAS), leave
+// out the partial-word code (FULLW), take phases of the Houdayer move (HOUD) or pair the
+// two chains' partial last words in one word (PAIR); see the kernel's comment.
 // The sweep is integer-only: per site, 2d unsatisfied-bond planes
 // (s_i ^ s_nb ^ J), a bit-sliced count u of them per replica (lane), auto-accept where
 // u >= d (dE = 4(d - u) <= 0), else accept iff the replica's Philox word is below
