@@ -252,3 +252,17 @@ def test_houdayer_low_slots_mcs_3d(oracle_mod, multi):
     kw = dict(ndim=3, dims=(8, 8, 8), n_samples=2, n_chains=2, temps=geometric_temps(0.5, 2.5, 12), sim_seed=29,
               houdayer=2 if multi else True, houdayer_slots=4)
     run_pair(oracle_mod, kw, ["m"] * 8)
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_houdayer_low_slots_multi_mcs_calls(oracle_mod, multi):
+    """The move kept to 4 of 12 slots, in calls of several MCS: between two moves the
+    sweep launch also takes the previous move's flips, the energies and the exchange."""
+    kw = dict(ndim=3, dims=(8, 8, 8), n_samples=2, n_chains=2, temps=geometric_temps(0.5, 2.5, 12), sim_seed=31,
+              houdayer=2 if multi else True, houdayer_slots=4)
+    sim, orc = gpu_of(**kw), oracle_of(oracle_mod, **_okw(kw))
+    for t, n in enumerate((3, 1, 4)):
+        sim.run_mcs(n)
+        orc.mcs(n, houdayer=kw["houdayer"])
+        assert_same_state(sim, orc, f"call {t} ({n} MCS)")
+    assert sim.counters()["houdayer_sites"] == orc.counters()["houd_flipped"]
